@@ -1,0 +1,486 @@
+"""FP64 CPU oracle for the 2D nonseparable discrete LCT (Pei & Huang,
+"Two-dimensional nonseparable discrete linear canonical transform based on
+CM-CC-CM-CC decomposition").
+
+TEST INFRASTRUCTURE ONLY. Nothing on the product path imports, calls or links
+this module: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference legs of ``bench.py`` may use it. It shares no code with the CUDA path.
+
+What it computes, in the paper's own terms and order, as plain direct sums in
+float64/complex128 (no FFT anywhere):
+
+* ``cm``     -- 2D discrete chirp multiplication, Eq. BasicCM12 (Sec. 2.A).
+* ``dft2`` / ``idft2`` -- 2D DFT / IDFT with the constant of Eqs. BasicDFT16/20
+                (Sec. 2.B), evaluated as dense DFT-matrix products whose phases
+                are reduced exactly as integers ((p*m) mod N) before ``exp``.
+* ``cc``     -- 2D discrete chirp convolution F^-1 CM^{-B} F, Eq. BasicCC20 (Sec. 2.C).
+* ``decompose`` -- the CM-CC-CM-CC factors of Eq. Bnonsym08 (Sec. 4.B):
+                B' = B - AH, D' = D - CH, C2 = B'^-1 (A - I), C1 = (D' - I) B'^-1.
+* ``forward`` -- the HA-NsDLCT chain of Eq. HA28, applied right to left:
+                CC^H, then CM^{C2}, then CC^{B'}, then CM^{C1}.
+* ``inverse`` -- the reversed chain with negated chirp matrices, Eq. CCCMCCCM04/30.
+* ``ha_search`` -- a solver for the H criterion of Eq. HA24 (the paper names none).
+* ``lc_h``    -- the closed-form one-parameter H of Eqs. LC04-LC10.
+* ``direct``  -- the sampled continuous kernel ("direct method"), Eq. Intro32.
+* ``project_sp4`` -- nearest-symplectic clean-up of 4-decimal printed matrices.
+
+Readings taken where the paper is silent or ambiguous (all listed in the design doc):
+
+1. Index origin: samples are centred, m = i - floor(N/2) for storage index i;
+   the same centred range is used for output and frequency indices.
+2. F^-1 carries the constant (d_in_x * d_in_y) / (j 2 pi) built from ITS OWN
+   input spacing (the frequency spacing 2 pi / (N dx)), so that CC^0 = -I and
+   the chain is unitary (the paper states the matrix L of Eq. self12 is unitary).
+3. All four operators are always executed, even when H = 0.
+4. Output sampling equals input sampling (du = dx, dv = dy, Sec. 2.A).
+5. Chirp matrices derived in floating point are symmetrised, c12 := (C12+C21)/2.
+6. H search: grid + compass on the feasible plane (see ``ha_search``).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+# --------------------------------------------------------------------------
+# ABCD helpers (Eqs. Intro04, Intro12, Intro16)
+# --------------------------------------------------------------------------
+
+
+def split_abcd(m):
+    """Return the 2x2 blocks A, B, C, D of a row-major 4x4 ABCD matrix (Eq. Intro04)."""
+    m = np.asarray(m, dtype=np.float64).reshape(4, 4)
+    return m[:2, :2].copy(), m[:2, 2:].copy(), m[2:, :2].copy(), m[2:, 2:].copy()
+
+
+def symplectic_form():
+    """J = (0, I; -I, 0)."""
+    j = np.zeros((4, 4))
+    j[:2, 2:] = np.eye(2)
+    j[2:, :2] = -np.eye(2)
+    return j
+
+
+def symplectic_residual(m) -> float:
+    """max |M^T J M - J|: zero exactly when the six constraints of Eq. Intro16 hold."""
+    m = np.asarray(m, dtype=np.float64).reshape(4, 4)
+    j = symplectic_form()
+    return float(np.max(np.abs(m.T @ j @ m - j)))
+
+
+def project_sp4(m, iters: int = 60):
+    """Move a nearly symplectic matrix onto Sp(4).
+
+    The paper prints its example matrices (Eqs. Acc24, Acc28, Add24, Add28) to
+    four decimals, so they violate Eq. Intro12 by up to ~1e-3. The iteration
+    X <- (X + J^T X^{-T} J) / 2 has every symplectic matrix as a fixed point
+    (for symplectic X, J^T X^{-T} J = X) and converges quadratically from a
+    nearby start.
+    """
+    x = np.asarray(m, dtype=np.float64).reshape(4, 4).copy()
+    j = symplectic_form()
+    for _ in range(iters):
+        x_new = 0.5 * (x + j.T @ np.linalg.inv(x).T @ j)
+        if np.max(np.abs(x_new - x)) < 1e-17:
+            x = x_new
+            break
+        x = x_new
+    return x
+
+
+# --------------------------------------------------------------------------
+# Basic discrete operators (Sec. 2)
+# --------------------------------------------------------------------------
+
+
+def centered(n: int) -> np.ndarray:
+    """Centred integer indices m = i - floor(N/2), i = 0..N-1 (reading 1)."""
+    return np.arange(n, dtype=np.int64) - n // 2
+
+
+def dft_matrix(n: int, sign: int) -> np.ndarray:
+    """W[p, m] = exp(sign * j 2 pi (p m) / N) over centred p, m.
+
+    The integer product p*m is reduced modulo N exactly before the exponential,
+    so every entry is one of the N roots of unity computed from a small angle.
+    """
+    p = centered(n)
+    e = np.mod(np.outer(p, p), n)
+    return np.exp(sign * 1j * TWO_PI * e / n)
+
+
+def cm(g: np.ndarray, c, du: float, dv: float) -> np.ndarray:
+    """2D discrete chirp multiplication CM^C, Eq. BasicCM12 (Sec. 2.A).
+
+    G[p,q] = exp(j/2 (c11 p^2 du^2 + 2 c12 p q du dv + c22 q^2 dv^2)) g[p,q]
+    with centred p, q and the input's own sampling intervals du, dv.
+    """
+    c = np.asarray(c, dtype=np.float64)
+    c11, c12, c22 = c[0, 0], 0.5 * (c[0, 1] + c[1, 0]), c[1, 1]
+    nx, ny = g.shape
+    p = centered(nx).astype(np.float64)[:, None] * du
+    q = centered(ny).astype(np.float64)[None, :] * dv
+    phase = 0.5 * (c11 * p * p + 2.0 * c12 * p * q + c22 * q * q)
+    return np.exp(1j * phase) * g
+
+
+def dft2(g: np.ndarray, dx: float, dy: float) -> np.ndarray:
+    """2D DFT F_{x,y} of Eq. BasicDFT16: (dx dy / (j 2 pi)) sum e^{-j2pi(pm+qn)/N} g[m,n]."""
+    nx, ny = g.shape
+    wx = dft_matrix(nx, -1)
+    wy = dft_matrix(ny, -1)
+    return (dx * dy / (1j * TWO_PI)) * (wx @ g @ wy.T)
+
+
+def idft2(g: np.ndarray, du: float, dv: float) -> np.ndarray:
+    """2D IDFT F^-1_{x,y} of Eq. BasicDFT20 with the constant (du dv)/(j 2 pi)
+    built from its own input spacing du, dv (reading 2)."""
+    nx, ny = g.shape
+    wx = dft_matrix(nx, +1)
+    wy = dft_matrix(ny, +1)
+    return (du * dv / (1j * TWO_PI)) * (wx @ g @ wy.T)
+
+
+def freq_spacing(n: int, d: float) -> float:
+    """Output spacing of the DFT, du = 2 pi / (N dx) (Sec. 2.B)."""
+    return TWO_PI / (n * d)
+
+
+def cc(g: np.ndarray, b, dx: float, dy: float) -> np.ndarray:
+    """2D discrete chirp convolution CC^B = F^-1 CM^{-B} F, Eq. BasicCC20 (Sec. 2.C).
+
+    The chirp multiplication in the middle acts on the DFT output, whose
+    sampling intervals are 2 pi / (N dx) and 2 pi / (N dy).
+    """
+    nx, ny = g.shape
+    dwx, dwy = freq_spacing(nx, dx), freq_spacing(ny, dy)
+    spec = dft2(g, dx, dy)
+    spec = cm(spec, -np.asarray(b, dtype=np.float64), dwx, dwy)
+    return idft2(spec, dwx, dwy)
+
+
+# --------------------------------------------------------------------------
+# CM-CC-CM-CC decomposition (Sec. 4.B)
+# --------------------------------------------------------------------------
+
+
+def sym_part(x):
+    x = np.asarray(x, dtype=np.float64)
+    return 0.5 * (x + x.T)
+
+
+def decompose(m, h):
+    """Factors of Eq. Bnonsym08 for a symmetric H.
+
+    Returns dict with H, Bp (= B - AH, Eq. Bnonsym04), Dp (= D - CH),
+    C2 (= Bp^-1 (A - I), the CM applied second) and C1 (= (Dp - I) Bp^-1, the
+    CM applied last). C1 and C2 are symmetric in exact arithmetic when Bp is
+    (reading 5 symmetrises them).
+    """
+    a, b, c, d = split_abcd(m)
+    h = sym_part(h)
+    eye = np.eye(2)
+    bp = b - a @ h
+    dp = d - c @ h
+    bpi = np.linalg.inv(bp)
+    c2 = bpi @ (a - eye)
+    c1 = (dp - eye) @ bpi
+    return {"H": h, "Bp": sym_part(bp), "Dp": dp, "C1": sym_part(c1), "C2": sym_part(c2),
+            "Bp_asym": float(abs(bp[0, 1] - bp[1, 0])),
+            "C_asym": float(max(abs(c1[0, 1] - c1[1, 0]), abs(c2[0, 1] - c2[1, 0])))}
+
+
+def compose_factors(params):
+    """Product (I,0;C1,I)(I,Bp;0,I)(I,0;C2,I)(I,H;0,I) of Eq. Bnonsym08."""
+    eye = np.eye(2)
+    zero = np.zeros((2, 2))
+
+    def cmm(c):
+        return np.block([[eye, zero], [c, eye]])
+
+    def ccm(b):
+        return np.block([[eye, b], [zero, eye]])
+
+    return cmm(params["C1"]) @ ccm(params["Bp"]) @ cmm(params["C2"]) @ ccm(params["H"])
+
+
+def gamma(c) -> float:
+    """Space-bandwidth growth ratio of Eq. HA16 for a symmetric 2x2 matrix."""
+    c = np.asarray(c, dtype=np.float64)
+    c11, c12, c22 = abs(c[0, 0]), abs(0.5 * (c[0, 1] + c[1, 0])), abs(c[1, 1])
+    return (c11 + c12 + 1.0) * (c12 + c22 + 1.0)
+
+
+def ha_objective(m, h) -> float:
+    """Objective of Eq. HA24: gamma(C1) gamma(B') gamma(C2) gamma(H)."""
+    p = decompose(m, h)
+    return gamma(p["C1"]) * gamma(p["Bp"]) * gamma(p["C2"]) * gamma(p["H"])
+
+
+def feasible_plane(m):
+    """Linear condition on h = (h11, h12, h22) for B - AH to be symmetric
+    (the requirement B' = B'^T of Eq. Bnonsym32).
+
+    (B - AH)_12 = (B - AH)_21 gives  r . h = rhs  with
+    r = (-a21, a11 - a22, a12), rhs = b12 - b21.  Setting h12 = h22 = 0 or
+    h11 = h12 = 0 recovers Eqs. LC08 and LC10.
+    """
+    a, b, _, _ = split_abcd(m)
+    r = np.array([-a[1, 0], a[0, 0] - a[1, 1], a[0, 1]])
+    rhs = b[0, 1] - b[1, 0]
+    return r, rhs
+
+
+def h_from_vec(v):
+    return np.array([[v[0], v[1]], [v[1], v[2]]], dtype=np.float64)
+
+
+DET_FLOOR = 1e-3
+
+
+def _objective_vec(m, hv):
+    h = h_from_vec(hv)
+    a, b, c, d = split_abcd(m)
+    bp = b - a @ h
+    det = bp[0, 0] * bp[1, 1] - bp[0, 1] * bp[1, 0]
+    if not np.isfinite(det) or abs(det) < DET_FLOOR:
+        return math.inf
+    return ha_objective(m, h)
+
+
+def _grid_objective(m, hs):
+    """Vectorised Eq. HA24 objective for an array of h vectors (K, 3)."""
+    a, b, c, d = split_abcd(m)
+    h11, h12, h22 = hs[:, 0], hs[:, 1], hs[:, 2]
+    # B' = B - A H
+    bp11 = b[0, 0] - (a[0, 0] * h11 + a[0, 1] * h12)
+    bp12 = b[0, 1] - (a[0, 0] * h12 + a[0, 1] * h22)
+    bp21 = b[1, 0] - (a[1, 0] * h11 + a[1, 1] * h12)
+    bp22 = b[1, 1] - (a[1, 0] * h12 + a[1, 1] * h22)
+    # D' = D - C H
+    dp11 = d[0, 0] - (c[0, 0] * h11 + c[0, 1] * h12)
+    dp12 = d[0, 1] - (c[0, 0] * h12 + c[0, 1] * h22)
+    dp21 = d[1, 0] - (c[1, 0] * h11 + c[1, 1] * h12)
+    dp22 = d[1, 1] - (c[1, 0] * h12 + c[1, 1] * h22)
+    det = bp11 * bp22 - bp12 * bp21
+    ok = np.abs(det) >= DET_FLOOR
+    det = np.where(ok, det, 1.0)
+    i11, i12, i21, i22 = bp22 / det, -bp12 / det, -bp21 / det, bp11 / det
+    # C2 = B'^-1 (A - I)
+    am = a - np.eye(2)
+    c2_11 = i11 * am[0, 0] + i12 * am[1, 0]
+    c2_12 = i11 * am[0, 1] + i12 * am[1, 1]
+    c2_21 = i21 * am[0, 0] + i22 * am[1, 0]
+    c2_22 = i21 * am[0, 1] + i22 * am[1, 1]
+    # C1 = (D' - I) B'^-1
+    e11, e12, e21, e22 = dp11 - 1.0, dp12, dp21, dp22 - 1.0
+    c1_11 = e11 * i11 + e12 * i21
+    c1_12 = e11 * i12 + e12 * i22
+    c1_21 = e21 * i11 + e22 * i21
+    c1_22 = e21 * i12 + e22 * i22
+
+    def g(x11, x12, x21, x22):
+        s = np.abs(0.5 * (x12 + x21))
+        return (np.abs(x11) + s + 1.0) * (s + np.abs(x22) + 1.0)
+
+    obj = g(c1_11, c1_12, c1_21, c1_22) * g(bp11, bp12, bp21, bp22) * \
+        g(c2_11, c2_12, c2_21, c2_22) * g(h11, h12, h12, h22)
+    return np.where(ok, obj, np.inf)
+
+
+def ha_search(m, grid: int = 241, grid3: int = 41, step_min: float = 1e-10):
+    """Choose H by the high-accuracy criterion of Eq. HA24 (Sec. 4.B.1).
+
+    The paper gives the criterion, not a solver. This one:
+    1. restricts h = (h11, h12, h22) to the feasible plane r.h = rhs
+       (``feasible_plane``), parametrised h = h0 + s e1 + t e2 with h0 the
+       minimum-norm point and (e1, e2) an orthonormal basis of the plane's
+       direction space;
+    2. scans a ``grid`` x ``grid`` lattice over s, t in [-R, R],
+       R = 6 max(1, max|M|), discarding points with |det B'| < 1e-3;
+    3. refines the best lattice point by compass search (halving the step down
+       to ``step_min``); ties keep the earlier point.
+    If r = 0 the plane degenerates: with rhs = 0 every symmetric H is feasible
+    and a 3D lattice (``grid3``^3) plus compass search is used; otherwise no
+    symmetric H exists and ValueError is raised.
+    Returns the symmetric 2x2 H.
+    """
+    m = np.asarray(m, dtype=np.float64).reshape(4, 4)
+    r, rhs = feasible_plane(m)
+    rn = float(np.linalg.norm(r))
+    scale = 6.0 * max(1.0, float(np.max(np.abs(m))))
+    if rn > 1e-12:
+        h0 = r * (rhs / (rn * rn))
+        # orthonormal basis of the null space of r
+        _, _, vt = np.linalg.svd(r.reshape(1, 3))
+        basis = vt[1:3]  # rows orthogonal to r
+        s = np.linspace(-scale, scale, grid)
+        ss, tt = np.meshgrid(s, s, indexing="ij")
+        hs = h0[None, :] + ss.reshape(-1, 1) * basis[0][None, :] + tt.reshape(-1, 1) * basis[1][None, :]
+        obj = _grid_objective(m, hs)
+        k = int(np.argmin(obj))
+        if not np.isfinite(obj[k]):
+            raise ValueError("ha_search: no feasible H with |det B'| >= floor on the lattice")
+        coords = np.array([ss.reshape(-1)[k], tt.reshape(-1)[k]])
+        step = 2.0 * scale / (grid - 1)
+
+        def point(cv):
+            return h0 + cv[0] * basis[0] + cv[1] * basis[1]
+
+        dirs = [np.array([1.0, 0.0]), np.array([-1.0, 0.0]), np.array([0.0, 1.0]), np.array([0.0, -1.0])]
+    else:
+        if abs(rhs) > 1e-12:
+            raise ValueError("ha_search: B - AH cannot be symmetric for any symmetric H")
+        s = np.linspace(-scale, scale, grid3)
+        g1, g2, g3 = np.meshgrid(s, s, s, indexing="ij")
+        hs = np.stack([g1.reshape(-1), g2.reshape(-1), g3.reshape(-1)], axis=1)
+        obj = _grid_objective(m, hs)
+        k = int(np.argmin(obj))
+        if not np.isfinite(obj[k]):
+            raise ValueError("ha_search: no feasible H with |det B'| >= floor on the lattice")
+        coords = hs[k].copy()
+        step = 2.0 * scale / (grid3 - 1)
+
+        def point(cv):
+            return cv
+
+        dirs = [np.eye(3)[i] * sgn for i in range(3) for sgn in (1.0, -1.0)]
+    best = _objective_vec(m, point(coords))
+    while step > step_min:
+        moved = False
+        for dv in dirs:
+            cand = coords + step * dv
+            val = _objective_vec(m, point(cand))
+            if val < best:
+                best, coords, moved = val, cand, True
+                break
+        if not moved:
+            step *= 0.5
+    return h_from_vec(point(coords))
+
+
+def lc_h(m):
+    """Low-complexity H of Eqs. LC04-LC10 (Sec. 4.B.2).
+
+    Candidates: H = (h,0;0,0) with h = (b21 - b12)/a21 when a21 != 0, and
+    H = (0,0;0,h) with h = (b12 - b21)/a12 when a12 != 0. Candidates whose B'
+    is (numerically) singular are dropped; of the rest the one with the lower
+    Eq. HA24 objective is returned. Returns None when no candidate is valid
+    (the paper then falls back to the HA choice).
+    """
+    a, b, _, _ = split_abcd(m)
+    cands = []
+    if abs(a[1, 0]) > 1e-12:
+        cands.append(np.array([[(b[1, 0] - b[0, 1]) / a[1, 0], 0.0], [0.0, 0.0]]))
+    if abs(a[0, 1]) > 1e-12:
+        cands.append(np.array([[0.0, 0.0], [0.0, (b[0, 1] - b[1, 0]) / a[0, 1]]]))
+    best, best_obj = None, math.inf
+    for h in cands:
+        bp = b - a @ h
+        if abs(np.linalg.det(bp)) < DET_FLOOR:
+            continue
+        val = ha_objective(m, h)
+        if val < best_obj:
+            best, best_obj = h, val
+    return best
+
+
+def plan(m, h=None, method: str = "ha"):
+    """Decomposition parameters for ABCD ``m``: H from ``h`` if given, else by
+    the HA search (Eq. HA24) or the LC closed form (Eqs. LC08/LC10)."""
+    m = np.asarray(m, dtype=np.float64).reshape(4, 4)
+    if h is None:
+        if method == "lc":
+            h = lc_h(m)
+            if h is None:
+                h = ha_search(m)
+        else:
+            h = ha_search(m)
+    return decompose(m, h)
+
+
+# --------------------------------------------------------------------------
+# The NsDLCT chain (Sec. 4.B, Eq. HA28) and its exact inverse (Sec. 4.C)
+# --------------------------------------------------------------------------
+
+
+def forward(g, params, dx: float, dy: float) -> np.ndarray:
+    """HA-NsDLCT of Eq. HA28, applied right to left:
+    CC^H, then CM^{C2} with C2 = B'^-1(A - I), then CC^{B'}, then CM^{C1}
+    with C1 = (D' - I) B'^-1. Output spacing equals input spacing."""
+    x = np.asarray(g, dtype=np.complex128)
+    x = cc(x, params["H"], dx, dy)
+    x = cm(x, params["C2"], dx, dy)
+    x = cc(x, params["Bp"], dx, dy)
+    x = cm(x, params["C1"], dx, dy)
+    return x
+
+
+def inverse(big_g, params, dx: float, dy: float) -> np.ndarray:
+    """Inverse chain of Eq. CCCMCCCM04 (= Eq. CCCMCCCM30), applied right to left:
+    CM^{-C1}, then CC^{-B'}, then CM^{-C2}, then CC^{-H}."""
+    x = np.asarray(big_g, dtype=np.complex128)
+    x = cm(x, -params["C1"], dx, dy)
+    x = cc(x, -params["Bp"], dx, dy)
+    x = cm(x, -params["C2"], dx, dy)
+    x = cc(x, -params["H"], dx, dy)
+    return x
+
+
+def transform(g, m, dx: float, dy: float, h=None, method: str = "ha"):
+    """Plan and apply the NsDLCT for ABCD ``m``."""
+    return forward(g, plan(m, h=h, method=method), dx, dy)
+
+
+# --------------------------------------------------------------------------
+# Direct method (Eq. Intro32) and error measures (Sec. 5)
+# --------------------------------------------------------------------------
+
+
+def direct(g, m, dx: float, dy: float, du: float, dv: float, nout_x: int, nout_y: int):
+    """Direct method of Eq. Intro32: the continuous kernel of Eq. Intro08
+    sampled at input points r = (m dx, n dy) and output points r' = (p du, q dv)
+    (all centred), summed with weight dx dy.
+
+    The cross term -2 r^T B^-1 r' is split per output row p, which turns the
+    O(N^4) sum into one matrix product per p; nothing is approximated.
+    The square root sqrt(-det B) is the principal complex root.
+    """
+    a, b, c, d = split_abcd(m)
+    bi = np.linalg.inv(b)
+    bia = bi @ a
+    dbi = d @ bi
+    nx, ny = g.shape
+    x = centered(nx) * dx
+    y = centered(ny) * dy
+    u = centered(nout_x) * du
+    v = centered(nout_y) * dv
+    xx, yy = x[:, None], y[None, :]
+    qin = np.exp(0.5j * (xx * bia[0, 0] * xx + xx * bia[0, 1] * yy + yy * bia[1, 0] * xx + yy * bia[1, 1] * yy))
+    uu, vv = u[:, None], v[None, :]
+    qout = np.exp(0.5j * (uu * dbi[0, 0] * uu + uu * dbi[0, 1] * vv + vv * dbi[1, 0] * uu + vv * dbi[1, 1] * vv))
+    h = qin * np.asarray(g, dtype=np.complex128)
+    # exp(-j r^T B^-1 r') = exp(-j (x bi11 u + x bi12 v + y bi21 u + y bi22 v))
+    vmat = np.exp(-1j * np.outer(v, y) * bi[1, 1])  # [q, n]
+    umat = np.exp(-1j * np.outer(v, x) * bi[0, 1])  # [q, m]
+    out = np.empty((nout_x, nout_y), dtype=np.complex128)
+    for ip, up in enumerate(u):
+        hp = h * np.exp(-1j * x * bi[0, 0] * up)[:, None] * np.exp(-1j * y * bi[1, 0] * up)[None, :]
+        z = hp @ vmat.T  # [m, q]
+        out[ip] = np.sum(umat * z.T, axis=1)
+    pref = dx * dy / (TWO_PI * np.sqrt(complex(-np.linalg.det(b))))
+    return pref * qout * out
+
+
+def nmse(approx, ref) -> float:
+    """Normalised mean-square error of Eqs. Acc04, Add16, Rev08."""
+    approx = np.asarray(approx)
+    ref = np.asarray(ref)
+    return float(np.sum(np.abs(approx - ref) ** 2) / np.sum(np.abs(ref) ** 2))
+
+
+def rel_l2(approx, ref) -> float:
+    """Relative L2 error ||approx - ref|| / ||ref||."""
+    return math.sqrt(nmse(approx, ref))
