@@ -1,0 +1,177 @@
+/*
+ * nslct.h -- C ABI of libnslct: the 2D nonseparable discrete linear canonical
+ * transform (NsDLCT) computed as the CM-CC-CM-CC chain of Pei & Huang
+ * ("Two-dimensional nonseparable discrete linear canonical transform based on
+ * CM-CC-CM-CC decomposition"), on NVIDIA GB300 (sm_103a).
+ *
+ * Problem statement followed (Sec. 2, first paragraph): an Nx x Ny input
+ * g[m,n] = g(m dx, n dy) sampled on a centred grid (m = i - floor(Nx/2) for
+ * storage row i, n = j - floor(Ny/2) for storage column j) is mapped to an
+ * Nx x Ny output G[p,q] ~ G(p du, q dv) with du = dx, dv = dy (Sec. 2.A),
+ * where G is the 2D NsLCT of Eq. Intro08 with the 4x4 ABCD matrix of
+ * Eq. Intro04.
+ *
+ * The transform is the chain of Eq. HA28 (Sec. 4.B.1), applied right to left:
+ *     CC^H  ->  CM^{C2}  ->  CC^{B'}  ->  CM^{C1}
+ * with B' = B - AH, D' = D - CH, C2 = B'^{-1}(A - I), C1 = (D' - I)B'^{-1}
+ * (Eq. Bnonsym08), CM the chirp multiplication of Eq. BasicCM12 and
+ * CC^B = F^{-1} CM^{-B} F the chirp convolution of Eq. BasicCC20.
+ *
+ * Data: every field is a dense row-major [Nx][Ny] array of interleaved complex
+ * values -- complex64 (float re, float im) for NSLCT_PREC_FP32 plans and
+ * complex128 (double re, double im) for NSLCT_PREC_FP64 plans -- in DEVICE
+ * memory of the device that was current when the plan was made. Row index i
+ * runs along x, column index j along y. Buffers are owned by the caller.
+ *
+ * Streams: nslct_stream_t is ABI-identical to cudaStream_t (pass one directly;
+ * NULL means the legacy default stream). Transform calls are asynchronous on
+ * that stream: they return after enqueueing the kernels.
+ *
+ * Errors: every entry point returns 0 (NSLCT_OK) or one of the NSLCT_E_*
+ * codes below; nslct_strerror() gives a static message. A call that fails
+ * enqueues nothing and leaves the output untouched.
+ *
+ * Thread safety: a plan may be used from several host threads at once for
+ * transforms on different output buffers; creating and destroying plans is
+ * not synchronised against use of the same plan.
+ */
+#ifndef NSLCT_H_
+#define NSLCT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nslct_plan_s* nslct_plan_t;   /* opaque, owned by the library */
+typedef struct CUstream_st* nslct_stream_t;  /* same type as cudaStream_t */
+
+/* ---- error codes ---------------------------------------------------------- */
+#define NSLCT_OK                0
+#define NSLCT_E_ARG             1  /* null pointer, N < 2, spacing <= 0, NaN input */
+#define NSLCT_E_NOT_SYMPLECTIC  2  /* ABCD violates Eq. Intro12 and no projection was asked */
+#define NSLCT_E_INFEASIBLE      3  /* no symmetric H with |det B'| >= 1e-3 (Eq. Bnonsym32) */
+#define NSLCT_E_SIZE            4  /* Nx or Ny not of the form 2^a 3^b with 8 <= N <= 4096, a >= 1, b <= 1 */
+#define NSLCT_E_CUDA            5  /* a CUDA runtime call failed */
+#define NSLCT_E_NOMEM           6  /* device or host allocation failed */
+#define NSLCT_E_TIMEOUT         7  /* a bounded device-side wait expired */
+#define NSLCT_E_UNSUPPORTED     8  /* flag combination not available */
+
+/* ---- plan flags ----------------------------------------------------------- */
+/* Choice of H (the free symmetric matrix of Eq. Bnonsym04). */
+#define NSLCT_H_HA          0x0u   /* high-accuracy criterion, Eq. HA24 (default) */
+#define NSLCT_H_LC          0x1u   /* low-complexity closed form, Eqs. LC08/LC10; HA if invalid */
+#define NSLCT_H_USER        0x2u   /* H given by the caller (nslct_plan_ex) */
+#define NSLCT_H_MASK        0x3u
+/* Replace a nearly symplectic ABCD (e.g. one printed to 4 decimals) by a
+ * nearby exactly symplectic one before planning. */
+#define NSLCT_PROJECT_SP4   0x10u
+/* Arithmetic of the transform. */
+#define NSLCT_PREC_FP32     0x000u /* complex64 data, FP32 FFT arithmetic (default) */
+#define NSLCT_PREC_FP64     0x100u /* complex128 data, FP64 arithmetic throughout */
+#define NSLCT_PREC_MASK     0xF00u
+
+/*
+ * nslct_plan -- derive the chain's parameters for one ABCD matrix and field size.
+ *
+ *   out      receives the new plan (set to NULL on failure).
+ *   abcd     16 doubles, row-major 4x4 (a11 a12 b11 b12 / a21 a22 b21 b22 /
+ *            c11 c12 d11 d12 / c21 c22 d21 d22), the layout of Eq. Intro04.
+ *            Must satisfy Eq. Intro12 to 1e-9 * max(1, max|M|^2) unless
+ *            NSLCT_PROJECT_SP4 is set.
+ *   Nx, Ny   field size (rows, columns); see NSLCT_E_SIZE for the sizes the GPU
+ *            path supports.
+ *   dx, dy   sampling intervals (> 0). The paper's condition for the DFT case
+ *            is dx^2 = 2 pi / Nx, dy^2 = 2 pi / Ny (Sec. 2.B).
+ *   flags    NSLCT_H_*, NSLCT_PROJECT_SP4, NSLCT_PREC_*.
+ *
+ * All derivation (symplectic check/projection, the H criterion of Eq. HA24 or
+ * the closed form of Eqs. LC08/LC10, B', D', C1, C2, fixed-point chirp
+ * coefficients) runs on the host in FP64. The plan allocates small device
+ * tables (twiddles) on the current device; it needs no per-call workspace.
+ */
+int nslct_plan(nslct_plan_t* out, const double abcd[16], int Nx, int Ny,
+               double dx, double dy, unsigned flags);
+
+/*
+ * nslct_plan_ex -- as nslct_plan; with NSLCT_H_USER, h_user (4 doubles,
+ * row-major 2x2, symmetrised) is used as H and must make B - AH symmetric
+ * (to 1e-9 relative) and invertible, else NSLCT_E_INFEASIBLE. h_user is
+ * ignored for the other NSLCT_H_* choices and may be NULL.
+ */
+int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny,
+                  double dx, double dy, unsigned flags, const double* h_user);
+
+/*
+ * nslct_derive -- the host-only part of planning, for inspection: validates
+ * (or projects) `abcd`, chooses H by `flags` (NSLCT_H_*; h_user as in
+ * nslct_plan_ex) and writes the projected ABCD (16 doubles), H, B' = B - AH,
+ * C1 = (D' - I)B'^{-1}, C2 = B'^{-1}(A - I) (4 doubles each, row-major) and the
+ * Eq. HA24 objective gamma(C1) gamma(B') gamma(C2) gamma(H) (Eq. HA16).
+ * Output pointers may be NULL. Touches no GPU. Same error codes as nslct_plan.
+ */
+int nslct_derive(const double abcd[16], unsigned flags, const double* h_user, double abcd_used[16],
+                 double H[4], double Bp[4], double C1[4], double C2[4], double* objective);
+
+/*
+ * nslct_plan_params -- copy out the plan's decomposition (Eq. Bnonsym08):
+ * H, B' = B - AH, C1 = (D' - I)B'^{-1} (the CM applied last) and
+ * C2 = B'^{-1}(A - I) (the CM applied second), each 4 doubles row-major.
+ * Any output pointer may be NULL. `field` must be 0 for single plans.
+ */
+int nslct_plan_params(nslct_plan_t plan, int field, double H[4], double Bp[4],
+                      double C1[4], double C2[4]);
+
+/*
+ * nslct_plan_info -- field size, precision flag and the projected ABCD the plan
+ * uses (abcd may be NULL).
+ */
+int nslct_plan_info(nslct_plan_t plan, int* Nx, int* Ny, unsigned* flags, double abcd[16]);
+
+/*
+ * nslct_forward -- out = L in, the NsDLCT of Eq. HA28.
+ *   in, out  device buffers of Nx*Ny complex elements (see "Data" above).
+ *            in == out (in-place) is allowed; otherwise they must not overlap.
+ *            `out` doubles as the chain's intermediate storage, so no
+ *            workspace is allocated.
+ * Five kernel passes are enqueued on `stream`.
+ */
+int nslct_forward(nslct_plan_t plan, const void* in, void* out, nslct_stream_t stream);
+
+/*
+ * nslct_inverse -- out = L^{-1} in, the chain of Eq. CCCMCCCM04 (= Eq.
+ * CCCMCCCM30): the forward chain reversed with every chirp matrix negated, which
+ * inverts it exactly in exact arithmetic (Sec. 4.D). Same buffer rules as
+ * nslct_forward. Because L is unitary (Sec. 6.B), this is also L^H.
+ */
+int nslct_inverse(nslct_plan_t plan, const void* in, void* out, nslct_stream_t stream);
+
+/*
+ * nslct_forward_pass -- enqueue ONE of the five kernel passes that make up
+ * nslct_forward, for profiling and per-pass testing; calling passes 0..4 in
+ * order on the same buffers gives exactly nslct_forward's result.
+ *   pass 0: row FFT of `in` (row-major) into `out` (2x2-tiled layout)
+ *   pass 1: column FFT, chirp CM^{-H} at the frequency spacing, column IFFT
+ *   pass 2: row IFFT, -1/(Nx Ny), CM^{C2}, row FFT
+ *   pass 3: column FFT, chirp CM^{-B'}, column IFFT
+ *   pass 4: row IFFT, -1/(Nx Ny), CM^{C1}, back to row-major in `out`
+ * Passes 1..4 read and write `out` only (`in` must still be non-NULL).
+ */
+int nslct_forward_pass(nslct_plan_t plan, int pass, const void* in, void* out, nslct_stream_t stream);
+
+/* nslct_destroy -- free a plan and its device tables (NULL is allowed). */
+int nslct_destroy(nslct_plan_t plan);
+
+/* nslct_strerror -- static description of an NSLCT_* code. */
+const char* nslct_strerror(int code);
+
+/* nslct_version -- library version string. */
+const char* nslct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSLCT_H_ */

@@ -34,7 +34,8 @@ Readings taken where the paper is silent or ambiguous (all listed in the design doc):
 3. All four operators are always executed, even when H = 0.
 4. Output sampling equals input sampling (du = dx, dv = dy, Sec. 2.A).
 5. Chirp matrices derived in floating point are symmetrised, c12 := (C12+C21)/2.
-6. H search: grid + compass on the feasible plane (see ``ha_search``).
+6. H search: lattice + shrinking-window refinement on the feasible plane
+   (see ``ha_search``).
 """
 from __future__ import annotations
 
@@ -290,7 +291,8 @@ def _grid_objective(m, hs):
     return np.where(ok, obj, np.inf)
 
 
-def ha_search(m, grid: int = 241, grid3: int = 41, step_min: float = 1e-10):
+def ha_search(m, grid: int = 241, grid3: int = 41, starts: int = 6, zoom_pts: int = 21,
+              tol: float = 1e-11):
     """Choose H by the high-accuracy criterion of Eq. HA24 (Sec. 4.B.1).
 
     The paper gives the criterion, not a solver. This one:
@@ -300,12 +302,16 @@ def ha_search(m, grid: int = 241, grid3: int = 41, step_min: float = 1e-10):
        direction space;
     2. scans a ``grid`` x ``grid`` lattice over s, t in [-R, R],
        R = 6 max(1, max|M|), discarding points with |det B'| < 1e-3;
-    3. refines the best lattice point by compass search (halving the step down
-       to ``step_min``); ties keep the earlier point.
+    3. refines each of the ``starts`` best lattice points (taken at least two
+       lattice steps apart) by a shrinking-window search: a ``zoom_pts`` x
+       ``zoom_pts`` grid around the current point, re-centred on its best
+       entry, with the window quartered each round until it is below ``tol``.
+       A full window (not a compass) is used because the objective has kinks
+       (absolute values in Eq. HA16) along which axis moves stall.
     If r = 0 the plane degenerates: with rhs = 0 every symmetric H is feasible
-    and a 3D lattice (``grid3``^3) plus compass search is used; otherwise no
-    symmetric H exists and ValueError is raised.
-    Returns the symmetric 2x2 H.
+    and the same is done in three dimensions (``grid3`` lattice, 9^3 windows);
+    otherwise no symmetric H exists and ValueError is raised.
+    Returns the symmetric 2x2 H with the lowest objective found.
     """
     m = np.asarray(m, dtype=np.float64).reshape(4, 4)
     r, rhs = feasible_plane(m)
@@ -313,52 +319,55 @@ def ha_search(m, grid: int = 241, grid3: int = 41, step_min: float = 1e-10):
     scale = 6.0 * max(1.0, float(np.max(np.abs(m))))
     if rn > 1e-12:
         h0 = r * (rhs / (rn * rn))
-        # orthonormal basis of the null space of r
         _, _, vt = np.linalg.svd(r.reshape(1, 3))
-        basis = vt[1:3]  # rows orthogonal to r
-        s = np.linspace(-scale, scale, grid)
-        ss, tt = np.meshgrid(s, s, indexing="ij")
-        hs = h0[None, :] + ss.reshape(-1, 1) * basis[0][None, :] + tt.reshape(-1, 1) * basis[1][None, :]
-        obj = _grid_objective(m, hs)
-        k = int(np.argmin(obj))
-        if not np.isfinite(obj[k]):
-            raise ValueError("ha_search: no feasible H with |det B'| >= floor on the lattice")
-        coords = np.array([ss.reshape(-1)[k], tt.reshape(-1)[k]])
-        step = 2.0 * scale / (grid - 1)
+        basis = vt[1:3]  # orthonormal rows orthogonal to r
+        dim = 2
+        lat = np.linspace(-scale, scale, grid)
+        coords = np.stack(np.meshgrid(lat, lat, indexing="ij"), axis=-1).reshape(-1, 2)
 
-        def point(cv):
-            return h0 + cv[0] * basis[0] + cv[1] * basis[1]
-
-        dirs = [np.array([1.0, 0.0]), np.array([-1.0, 0.0]), np.array([0.0, 1.0]), np.array([0.0, -1.0])]
+        def points(c):
+            return h0[None, :] + c[:, 0:1] * basis[0][None, :] + c[:, 1:2] * basis[1][None, :]
+        step0 = lat[1] - lat[0]
+        wpts = zoom_pts
     else:
         if abs(rhs) > 1e-12:
             raise ValueError("ha_search: B - AH cannot be symmetric for any symmetric H")
-        s = np.linspace(-scale, scale, grid3)
-        g1, g2, g3 = np.meshgrid(s, s, s, indexing="ij")
-        hs = np.stack([g1.reshape(-1), g2.reshape(-1), g3.reshape(-1)], axis=1)
-        obj = _grid_objective(m, hs)
-        k = int(np.argmin(obj))
-        if not np.isfinite(obj[k]):
-            raise ValueError("ha_search: no feasible H with |det B'| >= floor on the lattice")
-        coords = hs[k].copy()
-        step = 2.0 * scale / (grid3 - 1)
+        dim = 3
+        lat = np.linspace(-scale, scale, grid3)
+        coords = np.stack(np.meshgrid(lat, lat, lat, indexing="ij"), axis=-1).reshape(-1, 3)
 
-        def point(cv):
-            return cv
-
-        dirs = [np.eye(3)[i] * sgn for i in range(3) for sgn in (1.0, -1.0)]
-    best = _objective_vec(m, point(coords))
-    while step > step_min:
-        moved = False
-        for dv in dirs:
-            cand = coords + step * dv
-            val = _objective_vec(m, point(cand))
-            if val < best:
-                best, coords, moved = val, cand, True
-                break
-        if not moved:
-            step *= 0.5
-    return h_from_vec(point(coords))
+        def points(c):
+            return c
+        step0 = lat[1] - lat[0]
+        wpts = 9
+    obj = _grid_objective(m, points(coords))
+    order = np.argsort(obj, kind="stable")
+    if not np.isfinite(obj[order[0]]):
+        raise ValueError("ha_search: no feasible H with |det B'| >= floor on the lattice")
+    seeds = []
+    for k in order:
+        if not np.isfinite(obj[k]) or len(seeds) >= starts:
+            break
+        c = coords[k]
+        if all(np.max(np.abs(c - s0)) > 2.5 * step0 for s0 in seeds):
+            seeds.append(c.copy())
+    offs1 = np.linspace(-1.0, 1.0, wpts)
+    offs = np.stack(np.meshgrid(*([offs1] * dim), indexing="ij"), axis=-1).reshape(-1, dim)
+    best_c, best_v = None, math.inf
+    for c in seeds:
+        cur = c.copy()
+        cur_v = float(_grid_objective(m, points(cur[None, :]))[0])
+        half = step0
+        while half > tol:
+            cand = cur[None, :] + half * offs
+            vals = _grid_objective(m, points(cand))
+            k = int(np.argmin(vals))
+            if vals[k] < cur_v:
+                cur, cur_v = cand[k].copy(), float(vals[k])
+            half *= 0.25
+        if cur_v < best_v:
+            best_c, best_v = cur, cur_v
+    return h_from_vec(points(best_c[None, :])[0])
 
 
 def lc_h(m):

@@ -1,0 +1,280 @@
+// C ABI of libnslct (declared in include/nslct.h).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "plan_math.h"
+
+using namespace nslct;
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename R>
+int upload_twiddles(int L, void** dev) {
+  struct C2 { R x, y; };
+  std::vector<C2> host(L);
+  for (int k = 0; k < L; ++k) {
+    const double a = kTwoPi * (double)k / (double)L;
+    host[k].x = (R)std::cos(a);
+    host[k].y = (R)(-std::sin(a));
+  }
+  if (cudaMalloc(dev, sizeof(C2) * L) != cudaSuccess) { *dev = nullptr; return NSLCT_E_NOMEM; }
+  if (cudaMemcpy(*dev, host.data(), sizeof(C2) * L, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(*dev);
+    *dev = nullptr;
+    return NSLCT_E_CUDA;
+  }
+  return NSLCT_OK;
+}
+
+void free_plan(nslct_plan_s* p) {
+  if (!p) return;
+  if (p->tw_y && p->tw_y != p->tw_x) cudaFree(p->tw_y);
+  if (p->tw_x) cudaFree(p->tw_x);
+  delete p;
+}
+
+int launch(const nslct_plan_s* p, bool col, const PassDesc& d, cudaStream_t s) {
+  return p->prec == 1 ? launch_pass_f64(col, d, s) : launch_pass_f32(col, d, s);
+}
+
+// Enqueue passes [first, last] of the forward (or inverse) chain.
+int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, bool inverse, int first = 0,
+              int last = 4) {
+  if (!p || !in || !out || first < 0 || last > 4 || first > last) return NSLCT_E_ARG;
+  DeviceGuard g(p->device);
+  if (!g.ok) return NSLCT_E_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const double ccs = -1.0 / ((double)p->Nx * (double)p->Ny);  // each CC's constant, Eq. BasicDFT16/20
+  PassDesc base{};
+  base.Nx = p->Nx;
+  base.Ny = p->Ny;
+  base.scale = 1.0;
+
+  PassDesc d[5];
+  for (auto& x : d) x = base;
+  // pass 1: row pass, caller layout -> tiled layout in `out`
+  d[0].in = in; d[0].out = out; d[0].in_tiled = 0; d[0].out_tiled = 1; d[0].tw = p->tw_y;
+  // passes 2..4 in place on the tiled field; pass 5 back to the caller layout
+  for (int k = 1; k < 5; ++k) { d[k].in = out; d[k].out = out; d[k].in_tiled = 1; d[k].out_tiled = 1; }
+  d[4].out_tiled = 0;
+  d[1].tw = p->tw_x; d[2].tw = p->tw_y; d[3].tw = p->tw_x; d[4].tw = p->tw_y;
+  d[1].freq_domain = d[3].freq_domain = 1;
+  d[1].has_chirp = d[2].has_chirp = d[3].has_chirp = 1;
+  d[1].t1 = kFwd; d[1].t2 = kInv;
+  d[2].t1 = kInv; d[2].t2 = kFwd; d[2].scale = ccs;
+  d[3].t1 = kFwd; d[3].t2 = kInv;
+  d[4].t1 = kInv; d[4].scale = ccs;
+  if (!inverse) {
+    // CC^H, CM^{C2}, CC^{B'}, CM^{C1}  (Eq. HA28, right to left)
+    d[0].t1 = kFwd;
+    d[1].chirp = p->fwd_chi_h;
+    d[2].chirp = p->fwd_cm_c2;
+    d[3].chirp = p->fwd_chi_bp;
+    d[4].has_chirp = 1; d[4].chirp = p->fwd_cm_c1;
+  } else {
+    // CM^{-C1}, CC^{-B'}, CM^{-C2}, CC^{-H}  (Eq. CCCMCCCM04, right to left)
+    d[0].has_chirp = 1; d[0].chirp = p->inv_cm_c1; d[0].t2 = kFwd;
+    d[1].chirp = p->inv_chi_bp;
+    d[2].chirp = p->inv_cm_c2;
+    d[3].chirp = p->inv_chi_h;
+  }
+  const bool cols[5] = {false, true, false, true, false};
+  for (int k = first; k <= last; ++k) {
+    const int rc = launch(p, cols[k], d[k], s);
+    if (rc != NSLCT_OK) return rc;
+  }
+  return NSLCT_OK;
+}
+
+}  // namespace
+
+namespace nslct {
+bool supported_length(int L) {
+  switch (L) {
+    case 8: case 16: case 32: case 64: case 128: case 256: case 512: case 1024: case 2048: case 4096:
+    case 12: case 24: case 48: case 96: case 192: case 384: case 768: case 1536:
+      return true;
+    default:
+      return false;
+  }
+}
+}  // namespace nslct
+
+extern "C" {
+
+// Host-only part of planning: validation, H choice and decomposition.
+static int derive(const double abcd[16], unsigned flags, const double* h_user, double m[16], Decomp* dc) {
+  if (!abcd) return NSLCT_E_ARG;
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(abcd[i])) return NSLCT_E_ARG;
+  const unsigned hsel = flags & NSLCT_H_MASK;
+  if (hsel == 3u) return NSLCT_E_ARG;
+  if (hsel == NSLCT_H_USER && !h_user) return NSLCT_E_ARG;
+  std::memcpy(m, abcd, 16 * sizeof(double));
+  double mmax = 1.0;
+  for (int i = 0; i < 16; ++i) mmax = std::fmax(mmax, std::fabs(m[i]));
+  if (flags & NSLCT_PROJECT_SP4) {
+    if (!project_sp4(abcd, m)) return NSLCT_E_NOT_SYMPLECTIC;
+  }
+  if (symplectic_residual(m) > 1e-9 * mmax * mmax) return NSLCT_E_NOT_SYMPLECTIC;
+
+  Mat2 h{};
+  int rc = NSLCT_OK;
+  if (hsel == NSLCT_H_USER) {
+    for (int i = 0; i < 4; ++i)
+      if (!std::isfinite(h_user[i])) return NSLCT_E_ARG;
+    h = mat2_symmetrise({h_user[0], h_user[1], h_user[2], h_user[3]});
+    Mat2 a, b, c, d;
+    split_blocks(m, a, b, c, d);
+    const Mat2 bp = mat2_sub(b, mat2_mul(a, h));
+    double scale = 1.0;
+    for (double v : {bp.m00, bp.m01, bp.m10, bp.m11}) scale = std::fmax(scale, std::fabs(v));
+    if (std::fabs(bp.m01 - bp.m10) > 1e-9 * scale) return NSLCT_E_INFEASIBLE;
+  } else if (hsel == NSLCT_H_LC) {
+    rc = choose_h_lc(m, &h);
+    if (rc != NSLCT_OK) rc = choose_h_ha(m, &h);  // Sec. 4.B.2: fall back to the HA choice
+  } else {
+    rc = choose_h_ha(m, &h);
+  }
+  if (rc != NSLCT_OK) return rc;
+  *dc = decompose(m, h);
+  if (!(std::fabs(dc->det_bp) >= kDetFloor)) return NSLCT_E_INFEASIBLE;
+  return NSLCT_OK;
+}
+
+int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, double dx, double dy,
+                  unsigned flags, const double* h_user) {
+  if (!out) return NSLCT_E_ARG;
+  *out = nullptr;
+  if (!abcd || Nx < 2 || Ny < 2 || !(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
+    return NSLCT_E_ARG;
+  const unsigned prec_flag = flags & NSLCT_PREC_MASK;
+  if (prec_flag != NSLCT_PREC_FP32 && prec_flag != NSLCT_PREC_FP64) return NSLCT_E_UNSUPPORTED;
+  if (!supported_length(Nx) || !supported_length(Ny)) return NSLCT_E_SIZE;
+  double m[16];
+  Decomp dc{};
+  int rc = derive(abcd, flags, h_user, m, &dc);
+  if (rc != NSLCT_OK) return rc;
+
+  nslct_plan_s* p = new (std::nothrow) nslct_plan_s();
+  if (!p) return NSLCT_E_NOMEM;
+  p->Nx = Nx; p->Ny = Ny; p->dx = dx; p->dy = dy; p->flags = flags;
+  p->prec = prec_flag == NSLCT_PREC_FP64 ? 1 : 0;
+  std::memcpy(p->M, m, sizeof(m));
+  const Mat2* src[4] = {&dc.H, &dc.Bp, &dc.C1, &dc.C2};
+  double* dst[4] = {p->H, p->Bp, p->C1, p->C2};
+  for (int k = 0; k < 4; ++k) {
+    dst[k][0] = src[k]->m00; dst[k][1] = src[k]->m01; dst[k][2] = src[k]->m10; dst[k][3] = src[k]->m11;
+  }
+  fill_chirps(p);
+
+  if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return NSLCT_E_CUDA; }
+  rc = p->prec ? upload_twiddles<double>(Nx, &p->tw_x) : upload_twiddles<float>(Nx, &p->tw_x);
+  if (rc == NSLCT_OK) {
+    if (Ny == Nx) p->tw_y = p->tw_x;
+    else rc = p->prec ? upload_twiddles<double>(Ny, &p->tw_y) : upload_twiddles<float>(Ny, &p->tw_y);
+  }
+  if (rc == NSLCT_OK) rc = p->prec ? prepare_pass_f64(Nx) : prepare_pass_f32(Nx);
+  if (rc == NSLCT_OK && Ny != Nx) rc = p->prec ? prepare_pass_f64(Ny) : prepare_pass_f32(Ny);
+  if (rc != NSLCT_OK) { free_plan(p); return rc; }
+  *out = p;
+  return NSLCT_OK;
+}
+
+int nslct_derive(const double abcd[16], unsigned flags, const double* h_user, double abcd_used[16], double H[4],
+                 double Bp[4], double C1[4], double C2[4], double* objective) {
+  double m[16];
+  Decomp dc{};
+  const int rc = derive(abcd, flags, h_user, m, &dc);
+  if (rc != NSLCT_OK) return rc;
+  const Mat2* src[4] = {&dc.H, &dc.Bp, &dc.C1, &dc.C2};
+  double* dst[4] = {H, Bp, C1, C2};
+  for (int k = 0; k < 4; ++k) {
+    if (!dst[k]) continue;
+    dst[k][0] = src[k]->m00; dst[k][1] = src[k]->m01; dst[k][2] = src[k]->m10; dst[k][3] = src[k]->m11;
+  }
+  if (abcd_used) std::memcpy(abcd_used, m, sizeof(m));
+  if (objective) *objective = ha_objective(m, dc.H);
+  return NSLCT_OK;
+}
+
+int nslct_plan(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, double dx, double dy, unsigned flags) {
+  if ((flags & NSLCT_H_MASK) == NSLCT_H_USER) return NSLCT_E_ARG;
+  return nslct_plan_ex(out, abcd, Nx, Ny, dx, dy, flags, nullptr);
+}
+
+int nslct_plan_params(nslct_plan_t p, int field, double H[4], double Bp[4], double C1[4], double C2[4]) {
+  if (!p || field != 0) return NSLCT_E_ARG;
+  if (H) std::memcpy(H, p->H, 4 * sizeof(double));
+  if (Bp) std::memcpy(Bp, p->Bp, 4 * sizeof(double));
+  if (C1) std::memcpy(C1, p->C1, 4 * sizeof(double));
+  if (C2) std::memcpy(C2, p->C2, 4 * sizeof(double));
+  return NSLCT_OK;
+}
+
+int nslct_plan_info(nslct_plan_t p, int* Nx, int* Ny, unsigned* flags, double abcd[16]) {
+  if (!p) return NSLCT_E_ARG;
+  if (Nx) *Nx = p->Nx;
+  if (Ny) *Ny = p->Ny;
+  if (flags) *flags = p->flags;
+  if (abcd) std::memcpy(abcd, p->M, 16 * sizeof(double));
+  return NSLCT_OK;
+}
+
+int nslct_forward(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream) {
+  return run_chain(p, in, out, stream, false);
+}
+
+int nslct_inverse(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream) {
+  return run_chain(p, in, out, stream, true);
+}
+
+int nslct_forward_pass(nslct_plan_t p, int pass, const void* in, void* out, nslct_stream_t stream) {
+  if (pass < 0 || pass > 4) return NSLCT_E_ARG;
+  return run_chain(p, in, out, stream, false, pass, pass);
+}
+
+int nslct_destroy(nslct_plan_t p) {
+  if (!p) return NSLCT_OK;
+  DeviceGuard g(p->device);
+  free_plan(p);
+  return NSLCT_OK;
+}
+
+const char* nslct_strerror(int code) {
+  switch (code) {
+    case NSLCT_OK: return "success";
+    case NSLCT_E_ARG: return "invalid argument";
+    case NSLCT_E_NOT_SYMPLECTIC: return "ABCD matrix is not symplectic (Eq. Intro12)";
+    case NSLCT_E_INFEASIBLE: return "no symmetric H gives a symmetric invertible B' = B - AH";
+    case NSLCT_E_SIZE: return "unsupported field size (need 2^a or 3*2^a, 8..4096)";
+    case NSLCT_E_CUDA: return "CUDA runtime error";
+    case NSLCT_E_NOMEM: return "out of memory";
+    case NSLCT_E_TIMEOUT: return "bounded device wait expired";
+    case NSLCT_E_UNSUPPORTED: return "unsupported flag combination";
+    default: return "unknown error code";
+  }
+}
+
+const char* nslct_version(void) { return "nslct-gb300 0.1"; }
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Internal declarations shared by the host plan, the C-ABI and the kernel passes.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nslct.h"
+
+namespace nslct {
+
+// A quadratic chirp phase in turns, stored as Q0.64 fixed point:
+//   turns(a, b) = k11 a^2 + k12 a b + k22 b^2   (mod 1, exact in uint64 arithmetic)
+// where (a, b) are the integer indices along x and y of the domain the chirp
+// acts in (centred sample indices in space, centred bin indices in frequency).
+// Because a^2, a*b, b^2 are integers, only the fractional part of each real
+// coefficient matters, so the 64-bit wrap-around IS the reduction modulo 2*pi.
+struct Chirp {
+  uint64_t k11, k12, k22;
+};
+
+enum Transform : int { kNone = 0, kFwd = 1, kInv = 2 };
+
+// One kernel pass: a batch of 1D transforms of length L along one axis, each
+// optionally followed by a chirp multiply and a second 1D transform.
+//   row pass: lines are rows i (length Ny), elements are columns j
+//   col pass: lines are columns j (length Nx), elements are rows i
+// Layouts: 0 = row-major [Nx][Ny]; 1 = 2x2-tiled, element (i, j) at
+//   (i/2)*2*Ny + (j/2)*4 + (i%2)*2 + (j%2), which keeps a row pair AND a column
+//   pair of the field in whole 32-byte sectors.
+struct PassDesc {
+  const void* in;
+  void* out;
+  int Nx, Ny;
+  int in_tiled, out_tiled;
+  int t1, t2;          // Transform before / after the chirp
+  int has_chirp;
+  int freq_domain;     // chirp indices: 0 = centred samples, 1 = centred bins
+  Chirp chirp;
+  double scale;        // real factor applied with the chirp (or alone)
+  const void* tw;      // twiddle table of the pass axis length: tw[k] = e^{-2 pi i k / L}
+};
+
+// Enqueue one pass. `col` selects the axis. Returns an NSLCT_* code.
+int launch_pass_f32(bool col, const PassDesc& d, cudaStream_t s);
+int launch_pass_f64(bool col, const PassDesc& d, cudaStream_t s);
+// Prepare kernel attributes (dynamic shared memory) for length L on the current device.
+int prepare_pass_f32(int L);
+int prepare_pass_f64(int L);
+
+// True when L is a length the kernels are instantiated for.
+bool supported_length(int L);
+
+}  // namespace nslct
+
+// The opaque plan (one ABCD matrix, one field size).
+struct nslct_plan_s {
+  int Nx, Ny;
+  double dx, dy;
+  unsigned flags;
+  int prec;            // 0 = fp32, 1 = fp64
+  int device;
+  double M[16];        // the (possibly projected) ABCD matrix
+  double H[4], Bp[4], C1[4], C2[4];
+  // Forward chain chirps (application order): chi_H (frequency, -H),
+  // cm_C2 (space), chi_Bp (frequency, -B'), cm_C1 (space).
+  nslct::Chirp fwd_chi_h, fwd_cm_c2, fwd_chi_bp, fwd_cm_c1;
+  // Inverse chain chirps: cm_-C1, chi_+B', cm_-C2, chi_+H.
+  nslct::Chirp inv_cm_c1, inv_chi_bp, inv_cm_c2, inv_chi_h;
+  void* tw_x;          // device twiddles for length Nx
+  void* tw_y;          // device twiddles for length Ny (may alias tw_x)
+};
