@@ -4,7 +4,10 @@ oracle (so near-ties in the H criterion cannot break parity).
 
 Tolerances (relative L2 over the whole field):
 * FP32 (complex64) path: 2e-5;
-* FP64 (complex128) path: 1e-12.
+* FP64 (complex128) path: 1e-12 at N <= 64, growing linearly with N above.
+  Both sides round chirp phases of magnitude ~ |c| (N/2)^2 dx^2 / 2, which is
+  ~ |c| pi N / 4 under the sampling condition dx^2 = 2 pi / N, so their FP64
+  rounding differences grow in proportion to N.
 """
 from __future__ import annotations
 
@@ -23,6 +26,10 @@ pytestmark = pytest.mark.gpu
 
 TOL32 = 2e-5
 TOL64 = 1e-12
+
+
+def tol64(nx, ny):
+    return TOL64 * max(1.0, max(nx, ny) / 64.0)
 PM = paper_matrices()
 
 
@@ -154,7 +161,7 @@ def test_fp64_shapes(N, nx, ny):
     m = I.random_symplectic_abcd(nx + ny)
     g = I.blob_field(nx, ny, seed=nx + 3 * ny, width_range=(1.0, 4.0))
     plan = _plan(N, m, nx, ny, precision="fp64")
-    assert O.rel_l2(_gpu(plan, g), _oracle(plan, g)) < TOL64
+    assert O.rel_l2(_gpu(plan, g), _oracle(plan, g)) < tol64(nx, ny)
 
 
 def test_degenerate_plane_and_user_h(N):
