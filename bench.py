@@ -326,7 +326,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-abcd", type=int, default=16,
+                    help="ABCD matrices per step (16 is the benchmark workload; fewer only for profiling captures)")
     args = ap.parse_args()
+    global N_ABCD
+    N_ABCD = max(1, min(16, args.n_abcd))
     world, rank, local = _dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -5,6 +5,7 @@
 #include <new>
 #include <vector>
 
+#include "fft_schedule.h"
 #include "plan_math.h"
 
 using namespace nslct;
@@ -27,17 +28,25 @@ struct DeviceGuard {
   }
 };
 
+// Per-stage twiddle table of length L (layout in fft_schedule.h): for stage
+// st >= 1 with radix RD and NS earlier points, entry [jm][r] = W_{NS RD}^{jm r}.
 template <typename R>
 int upload_twiddles(int L, void** dev) {
   struct C2 { R x, y; };
-  std::vector<C2> host(L);
-  for (int k = 0; k < L; ++k) {
-    const double a = kTwoPi * (double)k / (double)L;
-    host[k].x = (R)std::cos(a);
-    host[k].y = (R)(-std::sin(a));
+  const int n = twiddle_table_size(L) > 0 ? twiddle_table_size(L) : 1;
+  std::vector<C2> host(n, C2{(R)1, (R)0});
+  for (int st = 1; st < num_stages(L); ++st) {
+    const int rd = stage_radix(L, st), ns = stage_ns(L, st), off = stage_table_offset(L, st);
+    for (int jm = 0; jm < ns; ++jm)
+      for (int r = 0; r < rd; ++r) {
+        const long num = (long)jm * r, den = (long)ns * rd;
+        const double a = kTwoPi * (double)(num % den) / (double)den;
+        host[off + jm * rd + r].x = (R)std::cos(a);
+        host[off + jm * rd + r].y = (R)(-std::sin(a));
+      }
   }
-  if (cudaMalloc(dev, sizeof(C2) * L) != cudaSuccess) { *dev = nullptr; return NSLCT_E_NOMEM; }
-  if (cudaMemcpy(*dev, host.data(), sizeof(C2) * L, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMalloc(dev, sizeof(C2) * n) != cudaSuccess) { *dev = nullptr; return NSLCT_E_NOMEM; }
+  if (cudaMemcpy(*dev, host.data(), sizeof(C2) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(*dev);
     *dev = nullptr;
     return NSLCT_E_CUDA;
@@ -60,6 +69,8 @@ int launch(const nslct_plan_s* p, bool col, const PassDesc& d, cudaStream_t s) {
 int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, bool inverse, int first = 0,
               int last = 4) {
   if (!p || !in || !out || first < 0 || last > 4 || first > last) return NSLCT_E_ARG;
+  // 16-byte copies need 16-byte aligned fields
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return NSLCT_E_ARG;
   DeviceGuard g(p->device);
   if (!g.ok) return NSLCT_E_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -96,6 +107,11 @@ int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, 
     d[1].chirp = p->inv_chi_bp;
     d[2].chirp = p->inv_cm_c2;
     d[3].chirp = p->inv_chi_h;
+  }
+  for (auto& x : d) {
+    x.fscale = (float)x.scale;
+    x.scale_only = (!x.has_chirp && x.scale != 1.0) ? 1 : 0;
+    x.num_sms = p->num_sms;
   }
   const bool cols[5] = {false, true, false, true, false};
   for (int k = first; k <= last; ++k) {
@@ -187,7 +203,11 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   }
   fill_chirps(p);
 
-  if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return NSLCT_E_CUDA; }
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    free_plan(p);
+    return NSLCT_E_CUDA;
+  }
   rc = p->prec ? upload_twiddles<double>(Nx, &p->tw_x) : upload_twiddles<float>(Nx, &p->tw_x);
   if (rc == NSLCT_OK) {
     if (Ny == Nx) p->tw_y = p->tw_x;

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "fft_schedule.h"
 
 namespace nslct {
 
@@ -193,43 +194,25 @@ template <typename R> struct Dft<R, 12> : DftComposite<R, 4, 3> {};
 template <typename R> struct Dft<R, 16> : DftComposite<R, 4, 4> {};
 template <typename R> struct Dft<R, 24> : DftComposite<R, 8, 3> {};
 
-// ---------------------------------------------------------------------------
-// per-length FFT schedule
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
-
-// elements per thread
-__host__ __device__ constexpr int elems_per_thread(int L) {
-  return is_pow2(L) ? (L >= 16 ? 16 : L) : (L >= 24 ? 24 : L);
-}
-// radix of stage `st`: the largest allowed radix first, then powers of two
-__host__ __device__ constexpr int stage_radix(int L, int st) {
-  int rem = L;
-  int first = is_pow2(L) ? (L >= 16 ? 16 : L) : (L >= 24 ? 24 : L);
-  int r = first;
-  for (int i = 0; i <= st; ++i) {
-    if (i == 0) {
-      r = first;
-    } else {
-      int big = is_pow2(L) ? 16 : 8;
-      r = rem >= big ? big : rem;
-    }
-    if (i < st) rem /= r;
-  }
-  return r;
-}
-__host__ __device__ constexpr int num_stages(int L) {
-  int rem = L, s = 0;
-  while (rem > 1) { rem /= stage_radix(L, s); ++s; }
-  return s;
-}
-__host__ __device__ constexpr int stage_ns(int L, int st) {  // product of the radices before `st`
-  int ns = 1;
-  for (int i = 0; i < st; ++i) ns *= stage_radix(L, i);
-  return ns;
-}
-
 __device__ __forceinline__ int padded(int e) { return e + (e >> 4); }
+
+// Twiddles of stage ST for butterfly jm: tab[OFF + jm*RD + r] = W_{NS*RD}^{jm*r}.
+template <typename R, int RD>
+__device__ __forceinline__ void load_twiddles(const cpx<R>* __restrict__ row, cpx<R>* w) {
+  if constexpr (sizeof(R) == 4 && RD % 2 == 0) {
+    // two complex64 per 16-byte load; rows start at even entries
+    const float4* p4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int r = 0; r < RD; r += 2) {
+      const float4 q = __ldg(p4 + r / 2);
+      w[r] = mk<R>(q.x, q.y);
+      w[r + 1] = mk<R>(q.z, q.w);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < RD; ++r) w[r] = row[r];
+  }
+}
 
 template <typename R, int L, int P>
 struct LineFft {
@@ -262,9 +245,10 @@ struct LineFft {
       const int j = t + u * T_LINE;
       const int jm = j % NS;
       if constexpr (NS > 1) {
-        constexpr int STRIDE = L / (NS * RD);
+        cpx<R> w[RD];
+        load_twiddles<R, RD>(tw + stage_table_offset(L, ST) + jm * RD, w);
 #pragma unroll
-        for (int r = 1; r < RD; ++r) x[r] = cmul<R>(x[r], tw[jm * r * STRIDE]);
+        for (int r = 1; r < RD; ++r) x[r] = cmul<R>(x[r], w[r]);
       }
       Dft<R, RD>::run(x);
       if constexpr (LAST) {
@@ -313,7 +297,7 @@ __device__ __forceinline__ uint64_t chirp_turns(const Chirp& c, long long a, lon
 // e^{2 pi i turns} * scale; turns is a Q0.64 fraction of a full turn
 __device__ __forceinline__ float2 chirp_value(uint64_t q, float scale) {
   // top 32 bits as a signed fraction in [-1/2, 1/2)
-  const float tt = (float)(int)(q >> 32) * 2.3283064365386963e-10f;  // 2^-32
+  const float tt = (float)(int)(unsigned)(q >> 32) * 2.3283064365386963e-10f;  // 2^-32
   float s, c;
   __sincosf(6.28318530717958647692f * tt, &s, &c);
   return make_float2(c * scale, s * scale);
@@ -328,11 +312,57 @@ __device__ __forceinline__ double2 chirp_value(uint64_t q, double scale) {
 __device__ __forceinline__ int centred_bin(int b, int n) { return b < (n + 1) / 2 ? b : b - n; }
 
 // element (i, j) of an Nx x Ny field in the given layout
-__device__ __forceinline__ size_t elem_index(int i, int j, int Ny, int tiled) {
-  if (!tiled) return (size_t)i * Ny + j;
-  return (size_t)(i >> 1) * (2 * (size_t)Ny) + (size_t)(j >> 1) * 4 + (i & 1) * 2 + (j & 1);
+__device__ __forceinline__ int elem_index(int i, int j, int Ny, int tiled) {
+  if (!tiled) return i * Ny + j;
+  return (i >> 1) * (2 * Ny) + (j >> 1) * 4 + (i & 1) * 2 + (j & 1);
 }
 
+// Multiply the thread's E elements of line `line` by the pass chirp.
+// Element s sits at index e = t + T_LINE s along the line. The phase is a
+// quadratic in the element's integer coordinate a(s), which is linear in s
+// (centred samples: a = e - N/2; centred bins: a = e for e < N/2, e - N
+// after, and e < N/2 exactly when s < E/2 because N/2 is a multiple of
+// T_LINE). So the Q0.64 phase is advanced with two 64-bit additions per
+// element: q(s+1) = q(s) + D(s), D(s+1) = D(s) + 2 k T^2, all exact mod 2^64.
+template <typename R, int L, bool COL>
+__device__ __forceinline__ void apply_chirp(cpx<R>* v, const PassDesc& d, int t, int line, R scale) {
+  constexpr int E = elems_per_thread(L);
+  constexpr int T = L / E;
+  const int nl = COL ? d.Ny : d.Nx;   // length of the other axis
+  // coordinate of the line and of element 0
+  long long b, a0;
+  if (d.freq_domain) {
+    b = centred_bin(line, nl);
+    a0 = t;
+  } else {
+    b = (long long)line - nl / 2;
+    a0 = (long long)t - L / 2;
+  }
+  // phase = ka a^2 + kab a b + kb b^2 with (ka, kb) the element/line coefficients
+  const uint64_t ka = COL ? d.chirp.k11 : d.chirp.k22;
+  const uint64_t kb = COL ? d.chirp.k22 : d.chirp.k11;
+  const uint64_t kab_b = d.chirp.k12 * (uint64_t)b;
+  const uint64_t base = kb * (uint64_t)(b * b);
+  auto phase_at = [&](long long a) -> uint64_t { return ka * (uint64_t)(a * a) + kab_b * (uint64_t)a + base; };
+  const uint64_t dd = 2ull * ka * (uint64_t)((long long)T * T);
+  uint64_t q = phase_at(a0);
+  uint64_t dq = ka * (uint64_t)(2 * a0 * T + (long long)T * T) + kab_b * (uint64_t)T;
+#pragma unroll
+  for (int s = 0; s < E; ++s) {
+    if (d.freq_domain && s == E / 2) {
+      const long long a = a0 + (long long)T * s - L;
+      q = phase_at(a);
+      dq = ka * (uint64_t)(2 * a * T + (long long)T * T) + kab_b * (uint64_t)T;
+    }
+    v[s] = cmul<R>(v[s], chirp_value(q, scale));
+    q += dq;
+    dq += dd;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// v1: one panel per CTA, global loads straight into registers (FP64 plans)
+// ---------------------------------------------------------------------------
 template <typename R, int L> struct PassShape {
   static constexpr int E = elems_per_thread(L);
   static constexpr int T_LINE = L / E;
@@ -340,12 +370,12 @@ template <typename R, int L> struct PassShape {
   static constexpr int P0 = MAX_THREADS / T_LINE;
   static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);
   static constexpr int THREADS = T_LINE * P;
-  static constexpr int MIN_BLOCKS = sizeof(R) == 4 ? (THREADS >= 512 ? 2 : 1) : 1;
-  static constexpr size_t SMEM = (size_t)P * (L + L / 16) * sizeof(cpx<R>);
+  static constexpr int XSM = P * (L + L / 16);          // exchange buffer (complex entries)
+  static constexpr size_t SMEM = (size_t)XSM * sizeof(cpx<R>);
 };
 
 template <typename R, int L, bool COL>
-__global__ void __launch_bounds__(PassShape<R, L>::THREADS, PassShape<R, L>::MIN_BLOCKS)
+__global__ void __launch_bounds__(PassShape<R, L>::THREADS, 1)
 pass_kernel(PassDesc d) {
   using Sh = PassShape<R, L>;
   constexpr int E = Sh::E;
@@ -374,36 +404,13 @@ pass_kernel(PassDesc d) {
   }
 
   if (d.t1 != kNone) LineFft<R, L, P>::run(v, sm, t, p, tw, d.t1 == kInv);
-
   if (d.has_chirp) {
-    const R scale = (R)d.scale;
-    if (d.freq_domain) {
-      // column passes: a = bin along x (element), b = bin along y (line)
-      // row passes:    a = bin along x (line),    b = bin along y (element)
-      const long long lb = COL ? centred_bin(line, d.Ny) : centred_bin(line, d.Nx);
-#pragma unroll
-      for (int s = 0; s < E; ++s) {
-        const int e = t + T_LINE * s;
-        const long long eb = COL ? centred_bin(e, d.Nx) : centred_bin(e, d.Ny);
-        const uint64_t q = COL ? chirp_turns(d.chirp, eb, lb) : chirp_turns(d.chirp, lb, eb);
-        v[s] = cmul<R>(v[s], chirp_value(q, scale));
-      }
-    } else {
-      const long long lc = COL ? (long long)line - d.Ny / 2 : (long long)line - d.Nx / 2;
-#pragma unroll
-      for (int s = 0; s < E; ++s) {
-        const int e = t + T_LINE * s;
-        const long long ec = COL ? (long long)e - d.Nx / 2 : (long long)e - d.Ny / 2;
-        const uint64_t q = COL ? chirp_turns(d.chirp, ec, lc) : chirp_turns(d.chirp, lc, ec);
-        v[s] = cmul<R>(v[s], chirp_value(q, scale));
-      }
-    }
+    apply_chirp<R, L, COL>(v, d, t, line, (R)d.scale);
   } else if (d.scale != 1.0) {
     const R scale = (R)d.scale;
 #pragma unroll
     for (int s = 0; s < E; ++s) v[s] = mk<R>(v[s].x * scale, v[s].y * scale);
   }
-
   if (d.t2 != kNone) LineFft<R, L, P>::run(v, sm, t, p, tw, d.t2 == kInv);
 
   // In-place passes: every thread of the CTA must have loaded its inputs before
@@ -421,20 +428,156 @@ pass_kernel(PassDesc d) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// v2 (FP32): persistent CTAs, one per SM. The next panel is copied
+// global -> shared with 16-byte cp.async while the current one is in registers
+// going through the FFTs, so HBM reads overlap the arithmetic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int L, bool COL> struct PShape {
+  static constexpr int E = elems_per_thread(L);
+  static constexpr int T_LINE = L / E;
+  static constexpr int P0 = 512 / T_LINE;
+  static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);
+  static constexpr int THREADS = T_LINE * P;
+  static constexpr int XSM = P * (L + L / 16);                   // exchange buffer entries
+  static constexpr int STG = COL ? P * L : P * (L + 8);          // staging buffer entries (row-major rows padded)
+  static constexpr size_t SMEM = (size_t)(XSM + STG) * sizeof(float2);
+};
+
+// staging index of element e of panel line p
+template <int L, bool COL, int P>
+__device__ __forceinline__ int stg_index(int p, int e, int in_tiled) {
+  if (COL) return (e >> 1) * (2 * P) + (p >> 1) * 4 + (e & 1) * 2 + (p & 1);
+  if (in_tiled) return (p >> 1) * (2 * L) + (e >> 1) * 4 + (p & 1) * 2 + (e & 1);
+  return p * (L + 8) + e;
+}
+
+// Issue the 16-byte copies of one panel into the staging buffer.
+template <int L, bool COL>
+__device__ __forceinline__ void stage_panel(float2* stg, const float2* __restrict__ in, const PassDesc& d, int panel) {
+  using Sh = PShape<L, COL>;
+  constexpr int P = Sh::P;
+  constexpr int CHUNKS = P * L / 2;  // 16-byte chunks per panel
+  const int first = panel * P;
+  if (COL) {
+    // row pair a: P/2 tiles (2P complex, P chunks) starting at tile first/2
+    const int tiles_valid = min(P, d.Ny - first) / 2;
+    for (int c = threadIdx.x; c < CHUNKS; c += Sh::THREADS) {
+      const int a = c / P, k = c % P;
+      if ((k >> 1) < tiles_valid)
+        cp_async16(stg + a * (2 * P) + k * 2, in + a * (2 * d.Ny) + (first >> 1) * 4 + k * 2);
+    }
+  } else if (d.in_tiled) {
+    // P/2 row pairs, each 2L complex contiguous (L chunks)
+    const int rows_valid = min(P, d.Nx - first);
+    for (int c = threadIdx.x; c < CHUNKS; c += Sh::THREADS) {
+      const int q = c / L, k = c % L;
+      if (2 * q < rows_valid) cp_async16(stg + q * (2 * L) + k * 2, in + ((first >> 1) + q) * (2 * L) + k * 2);
+    }
+  } else {
+    constexpr int CPR = L / 2;  // chunks per row
+    const int rows_valid = min(P, d.Nx - first);
+    for (int c = threadIdx.x; c < CHUNKS; c += Sh::THREADS) {
+      const int p = c / CPR, k = c % CPR;
+      if (p < rows_valid) cp_async16(stg + p * (L + 8) + k * 2, in + (first + p) * L + k * 2);
+    }
+  }
+  cp_async_commit();
+}
+
+template <int L, bool COL>
+__global__ void __launch_bounds__(PShape<L, COL>::THREADS, 1)
+pass_kernel_v2(PassDesc d) {
+  using Sh = PShape<L, COL>;
+  constexpr int E = Sh::E;
+  constexpr int T_LINE = Sh::T_LINE;
+  constexpr int P = Sh::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* xs = reinterpret_cast<float2*>(smem_raw);
+  float2* stg = xs + Sh::XSM;
+
+  const int tid = threadIdx.x;
+  const int p = tid % P;
+  const int t = tid / P;
+  const int nlines = COL ? d.Ny : d.Nx;
+  const int npanels = (nlines + P - 1) / P;
+  const float2* __restrict__ in = reinterpret_cast<const float2*>(d.in);
+  float2* out = reinterpret_cast<float2*>(d.out);
+  const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
+  const float scale = d.fscale;
+
+  int panel = blockIdx.x;
+  if (panel < npanels) stage_panel<L, COL>(stg, in, d, panel);
+  for (; panel < npanels; panel += gridDim.x) {
+    const int line = panel * P + p;
+    const bool valid = line < nlines;
+    cp_async_wait_all();
+    __syncthreads();
+    float2 v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = stg[stg_index<L, COL, P>(p, t + T_LINE * s, d.in_tiled)];
+    __syncthreads();  // staging buffer free again
+    const int next = panel + gridDim.x;
+    if (next < npanels) stage_panel<L, COL>(stg, in, d, next);
+
+    if (d.t1 != kNone) LineFft<float, L, P>::run(v, xs, t, p, tw, d.t1 == kInv);
+    if (d.has_chirp) {
+      apply_chirp<float, L, COL>(v, d, t, line, scale);
+    } else if (d.scale_only) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = make_float2(v[s].x * scale, v[s].y * scale);
+    }
+    if (d.t2 != kNone) LineFft<float, L, P>::run(v, xs, t, p, tw, d.t2 == kInv);
+
+    if (valid) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const int e = t + T_LINE * s;
+        const int i = COL ? e : line;
+        const int j = COL ? line : e;
+        out[elem_index(i, j, d.Ny, d.out_tiled)] = v[s];
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
 template <typename R, int L, bool COL>
 inline int launch_one(const PassDesc& d, cudaStream_t s) {
-  using Sh = PassShape<R, L>;
   const int nlines = COL ? d.Ny : d.Nx;
-  const int blocks = (nlines + Sh::P - 1) / Sh::P;
-  pass_kernel<R, L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d);
+  if constexpr (sizeof(R) == 4) {
+    using Sh = PShape<L, COL>;
+    const int npanels = (nlines + Sh::P - 1) / Sh::P;
+    const int blocks = npanels < d.num_sms ? npanels : d.num_sms;
+    pass_kernel_v2<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d);
+  } else {
+    using Sh = PassShape<R, L>;
+    const int blocks = (nlines + Sh::P - 1) / Sh::P;
+    pass_kernel<R, L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d);
+  }
   return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
 }
 
 template <typename R, int L>
 inline int prepare_one() {
-  using Sh = PassShape<R, L>;
-  cudaError_t e1 = cudaFuncSetAttribute(pass_kernel<R, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-  cudaError_t e2 = cudaFuncSetAttribute(pass_kernel<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+  cudaError_t e1, e2;
+  if constexpr (sizeof(R) == 4) {
+    e1 = cudaFuncSetAttribute(pass_kernel_v2<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)PShape<L, false>::SMEM);
+    e2 = cudaFuncSetAttribute(pass_kernel_v2<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)PShape<L, true>::SMEM);
+  } else {
+    using Sh = PassShape<R, L>;
+    e1 = cudaFuncSetAttribute(pass_kernel<R, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+    e2 = cudaFuncSetAttribute(pass_kernel<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+  }
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? NSLCT_OK : NSLCT_E_CUDA;
 }
 

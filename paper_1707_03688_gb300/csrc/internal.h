@@ -37,7 +37,10 @@ struct PassDesc {
   int freq_domain;     // chirp indices: 0 = centred samples, 1 = centred bins
   Chirp chirp;
   double scale;        // real factor applied with the chirp (or alone)
-  const void* tw;      // twiddle table of the pass axis length: tw[k] = e^{-2 pi i k / L}
+  float fscale;        // the same factor in FP32
+  int scale_only;      // no chirp but scale != 1
+  int num_sms;         // persistent-grid size for the FP32 kernels
+  const void* tw;      // per-stage twiddle table of the pass axis length (see fft_schedule.h)
 };
 
 // Enqueue one pass. `col` selects the axis. Returns an NSLCT_* code.
@@ -66,6 +69,7 @@ struct nslct_plan_s {
   nslct::Chirp fwd_chi_h, fwd_cm_c2, fwd_chi_bp, fwd_cm_c1;
   // Inverse chain chirps: cm_-C1, chi_+B', cm_-C2, chi_+H.
   nslct::Chirp inv_cm_c1, inv_chi_bp, inv_cm_c2, inv_chi_h;
+  int num_sms;         // multiprocessors of `device`
   void* tw_x;          // device twiddles for length Nx
   void* tw_y;          // device twiddles for length Ny (may alias tw_x)
 };
