@@ -161,6 +161,102 @@ int nslct_inverse(nslct_plan_t plan, const void* in, void* out, nslct_stream_t s
  */
 int nslct_forward_pass(nslct_plan_t plan, int pass, const void* in, void* out, nslct_stream_t stream);
 
+/*
+ * nslct_backward -- vector-Jacobian product of y = L x (nslct_forward) for a
+ * real loss l(y), with gradients for the chain's parameters.
+ *   grad_out   dl/dRe y + j dl/dIm y (device, Nx*Ny elements of the plan's type)
+ *   y          the forward output L x (device, read only)
+ *   grad_in    receives dl/dRe x + j dl/dIm x = L^H grad_out (device). L is
+ *              unitary (Sec. 6.B), so this is the inverse chain of Eq.
+ *              CCCMCCCM04 applied to grad_out.
+ *   grad_theta NULL or a DEVICE pointer to 10 doubles: dl/dtheta for the
+ *              parametrisation M(theta) = (I,0;C,I)(L,0;0,L^-T)(I,B;0,I) of the
+ *              plan's ABCD, theta = (c11,c12,c22, l11,l12,l21,l22, b11,b12,b22)
+ *              (C, B symmetric, L = A), with H following theta as in
+ *              nslct_plan_theta. NSLCT_E_UNSUPPORTED if the plan's A is singular.
+ *   grad_chirp NULL or a DEVICE pointer to 12 doubles: dl/d(h11,h12,h22,
+ *              b'11,b'12,b'22, c1_11,c1_12,c1_22, c2_11,c2_12,c2_22) with the
+ *              decomposition of Eq. Bnonsym08 held fixed (off-diagonal entries
+ *              counted once, as they enter the chirp phases).
+ *   workspace  NULL, or a device buffer of Nx*Ny elements the call may
+ *              overwrite. With NULL, the plan makes one on the first call
+ *              (cudaMalloc) and keeps it until nslct_destroy.
+ * The forward intermediates are recomputed by running y back through the
+ * inverse chain next to grad_out, so nothing is stored by nslct_forward. On the
+ * first call with gradients the plan also allocates a small buffer of per-CTA
+ * partial sums. Calls on one plan that overlap on the GPU share those buffers
+ * and race. All device pointers must be 16-byte aligned.
+ */
+int nslct_backward(nslct_plan_t plan, const void* grad_out, const void* y, void* grad_in,
+                   double* grad_theta, double* grad_chirp, void* workspace, nslct_stream_t stream);
+
+/*
+ * nslct_plan_theta -- plan for M(theta) (see nslct_backward) with H = h0 moved
+ * onto the feasible plane of M(theta) along its normal:
+ *   h = h0 + r (rhs - r.h0) / (r.r),  r = (-a21, a11 - a22, a12), rhs = b12 - b21,
+ * the smooth H rule the parameter gradients differentiate. With h0 NULL, H is
+ * chosen by the Eq. HA24 criterion instead. The NSLCT_H_* and
+ * NSLCT_PROJECT_SP4 bits of `flags` are ignored; NSLCT_E_ARG if L is singular.
+ */
+int nslct_plan_theta(nslct_plan_t* out, const double theta[10], const double h0[4], int Nx, int Ny,
+                     double dx, double dy, unsigned flags);
+
+/* nslct_plan_theta_get -- theta of the plan's ABCD (NSLCT_E_UNSUPPORTED if A is singular). */
+int nslct_plan_theta_get(nslct_plan_t plan, double theta[10]);
+
+/* ---- batches of fields with uneven sizes ------------------------------------ */
+typedef struct nslct_batch_s* nslct_batch_t;  /* opaque, owned by the library */
+
+/*
+ * nslct_plan_batch -- plans for `nfields` fields, field f of size Nx[f] x Ny[f]
+ * with spacings dx[f], dy[f] and its own ABCD matrix abcd[16 f .. 16 f + 15]
+ * (layout as in nslct_plan). NSLCT_PREC_FP32 only. Line lengths must be one of
+ * 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 4096 (else
+ * NSLCT_E_SIZE). Each field gets its own plan (reachable by nslct_batch_plan);
+ * the batch also prepares per-pass work lists of (field, panel) items, longest
+ * lines first.
+ */
+int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const int* Nx, const int* Ny,
+                     const double* dx, const double* dy, unsigned flags);
+
+/* nslct_batch_size / nslct_batch_plan -- field count; the plan of field `field` (owned by the batch). */
+int nslct_batch_size(nslct_batch_t batch);
+int nslct_batch_plan(nslct_batch_t batch, int field, nslct_plan_t* plan);
+
+/*
+ * nslct_batch_bind -- attach the fields' device buffers: in[f], out[f] (host
+ * arrays of nfields device pointers; row-major fields as for nslct_forward,
+ * 16-byte aligned). Uploads the pass descriptors (synchronous) and drops any
+ * captured graph.
+ */
+int nslct_batch_bind(nslct_batch_t batch, const void* const* in, void* const* out);
+
+/*
+ * nslct_batch_forward -- out[f] = L_f in[f] for every bound field: one counter
+ * reset and five persistent launches, one per pass of the chain, each covering
+ * all fields (items handed out through an atomic counter); or, after
+ * nslct_batch_capture, one launch of the captured CUDA graph.
+ */
+int nslct_batch_forward(nslct_batch_t batch, nslct_stream_t stream);
+
+/* nslct_batch_capture -- capture the bound batch's launches on `stream` (not the
+ * legacy default stream) into a CUDA graph that nslct_batch_forward then launches. */
+int nslct_batch_capture(nslct_batch_t batch, nslct_stream_t stream);
+
+/* nslct_batch_forward_each -- the same transforms as per-field nslct_forward calls (5 launches per field). */
+int nslct_batch_forward_each(nslct_batch_t batch, nslct_stream_t stream);
+
+/* nslct_batch_destroy -- free the batch, its plans and its graph. */
+int nslct_batch_destroy(nslct_batch_t batch);
+
+/*
+ * nslct_status -- synchronise with the plan's device (blocking) and report
+ * whether any of its kernels gave up a bounded device-side wait since the last
+ * call: NSLCT_OK, or NSLCT_E_TIMEOUT (the status word is cleared). A kernel
+ * that gives up leaves its output incomplete instead of hanging the GPU.
+ */
+int nslct_status(nslct_plan_t plan);
+
 /* nslct_destroy -- free a plan and its device tables (NULL is allowed). */
 int nslct_destroy(nslct_plan_t plan);
 

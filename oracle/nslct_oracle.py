@@ -493,3 +493,181 @@ def nmse(approx, ref) -> float:
 def rel_l2(approx, ref) -> float:
     """Relative L2 error ||approx - ref|| / ||ref||."""
     return math.sqrt(nmse(approx, ref))
+
+
+# --------------------------------------------------------------------------
+# Gradients of a real loss through the chain (adjoint of Eq. HA28)
+# --------------------------------------------------------------------------
+#
+# Parameters. An ABCD matrix with invertible A is written as
+#   M(theta) = (I, 0; C, I) (L, 0; 0, L^-T) (I, B; 0, I) = (L, L B; C L, C L B + L^-T)
+# with C, B symmetric (3 + 3 entries) and L = A (4 entries): the 10 degrees of
+# freedom of Sec. 1 (Eq. Intro12 leaves 10 of 16). theta = (c11, c12, c22,
+# l11, l12, l21, l22, b11, b12, b22).
+# H(theta): a reference H0 moved onto the feasible plane of M(theta) along the
+# plane's normal, H0 + r (rhs - r.h0) / |r|^2 (smooth in theta; equals H0 when
+# H0 is feasible).
+
+
+def theta_from_abcd(m):
+    """theta of M: L = A, C = sym(C A^-1), B = sym(A^-1 B)."""
+    a, b, c, _ = split_abcd(m)
+    ai = np.linalg.inv(a)
+    cs = sym_part(c @ ai)
+    bs = sym_part(ai @ b)
+    return np.array([cs[0, 0], cs[0, 1], cs[1, 1], a[0, 0], a[0, 1], a[1, 0], a[1, 1],
+                     bs[0, 0], bs[0, 1], bs[1, 1]])
+
+
+def abcd_from_theta(th):
+    """(I,0;C,I)(L,0;0,L^-T)(I,B;0,I) for theta (works for complex theta)."""
+    th = np.asarray(th)
+    dt = np.result_type(th.dtype, np.float64)
+    c = np.array([[th[0], th[1]], [th[1], th[2]]], dtype=dt)
+    lm = np.array([[th[3], th[4]], [th[5], th[6]]], dtype=dt)
+    b = np.array([[th[7], th[8]], [th[8], th[9]]], dtype=dt)
+    eye = np.eye(2, dtype=dt)
+    z = np.zeros((2, 2), dtype=dt)
+    lit = np.linalg.inv(lm).T
+    return np.block([[eye, z], [c, eye]]) @ np.block([[lm, z], [z, lit]]) @ np.block([[eye, b], [z, eye]])
+
+
+def h_of_theta(th, h0):
+    """H0 moved along the normal r onto the feasible plane r.h = rhs of M(theta)."""
+    m = abcd_from_theta(th)
+    a, b = m[:2, :2], m[:2, 2:]
+    r = np.array([-a[1, 0], a[0, 0] - a[1, 1], a[0, 1]])
+    rhs = b[0, 1] - b[1, 0]
+    hv = np.array([h0[0, 0], 0.5 * (h0[0, 1] + h0[1, 0]), h0[1, 1]], dtype=r.dtype)
+    rr = r @ r  # no conjugate: analytic in theta (complex-step friendly)
+    if abs(rr) < 1e-24:
+        v = hv
+    else:
+        v = hv + r * (rhs - r @ hv) / rr
+    return np.array([[v[0], v[1]], [v[1], v[2]]])
+
+
+def _chirp_vec(th, h0):
+    """(H, B', C1, C2) symmetric entries (12 values) as functions of theta, in
+    the order h11 h12 h22, b'11 b'12 b'22, c1_11 c1_12 c1_22, c2_11 c2_12 c2_22."""
+    m = abcd_from_theta(th)
+    h = h_of_theta(th, h0)
+    a, b, c, d = m[:2, :2], m[:2, 2:], m[2:, :2], m[2:, 2:]
+    eye = np.eye(2)
+    bp = b - a @ h
+    dp = d - c @ h
+    bpi = np.linalg.inv(bp)
+    c2 = bpi @ (a - eye)
+    c1 = (dp - eye) @ bpi
+    out = []
+    for x in (h, bp, c1, c2):
+        out += [x[0, 0], 0.5 * (x[0, 1] + x[1, 0]), x[1, 1]]
+    return np.array(out)
+
+
+def chirp_jacobian(th, h0, step: float = 1e-30):
+    """d(chirp entries)/d(theta), 12 x 10, by the complex-step derivative
+    Im f(theta + i s e_k) / s: every operation in _chirp_vec is analytic, so the
+    result is exact to rounding (no subtraction error)."""
+    th = np.asarray(th, dtype=np.float64)
+    jac = np.zeros((12, 10))
+    for k in range(10):
+        tc = th.astype(np.complex128)
+        tc[k] += 1j * step
+        jac[:, k] = np.imag(_chirp_vec(tc, h0)) / step
+    return jac
+
+
+def params_from_theta(th, h0):
+    m = abcd_from_theta(np.asarray(th, dtype=np.float64))
+    return decompose(m, h_of_theta(np.asarray(th, dtype=np.float64), h0))
+
+
+def dft2_adj(g, dx, dy):
+    """Adjoint of dft2: conj(constant) * W^H g conj(W)^... (W symmetric)."""
+    nx, ny = g.shape
+    wx = dft_matrix(nx, +1)
+    wy = dft_matrix(ny, +1)
+    return np.conj(dx * dy / (1j * TWO_PI)) * (wx @ g @ wy.T)
+
+
+def idft2_adj(g, du, dv):
+    nx, ny = g.shape
+    wx = dft_matrix(nx, -1)
+    wy = dft_matrix(ny, -1)
+    return np.conj(du * dv / (1j * TWO_PI)) * (wx @ g @ wy.T)
+
+
+def _phase_weights(nx, ny, du, dv, sign):
+    """d phi / d(c11, c12, c22) of a chirp exp(j sign/2 (c11 p^2 du^2 + 2 c12 p q du dv + c22 q^2 dv^2))."""
+    p = centered(nx).astype(np.float64)[:, None] * du
+    q = centered(ny).astype(np.float64)[None, :] * dv
+    return (sign * 0.5 * p * p * np.ones((1, ny)), sign * p * q, sign * 0.5 * q * q * np.ones((nx, 1)))
+
+
+def chain_vjp(x, gbar, params, dx, dy, with_abs: bool = False):
+    """Gradient of a real loss l(y), y = forward(x), given gbar = dl/dRe y + j dl/dIm y.
+
+    Returns (grad_x, grad_chirp[, abs_chirp]) where grad_x = L^H gbar and grad_chirp holds
+    dl/d(h11, h12, h22, b'11, b'12, b'22, c1_11, c1_12, c1_22, c2_11, c2_12, c2_22)
+    (symmetric off-diagonal entries counted once, as they enter the phases).
+    Every chirp stage v_out = e^{j phi(c)} v_in contributes
+    dl/dc = Re sum conj(gbar_s) j (dphi/dc) v_out = -sum (dphi/dc) Im(conj(gbar_s) v_out),
+    where gbar_s is gbar pulled back through the later stages by their adjoints.
+    With ``with_abs`` also returns sum |dphi/dc| |gbar_s| |v_out| per entry: the
+    scale against which rounding in the fields (not in this sum) is measured.
+    """
+    nx, ny = x.shape
+    dwx, dwy = freq_spacing(nx, dx), freq_spacing(ny, dy)
+    x = np.asarray(x, dtype=np.complex128)
+    # forward, keeping each chirp stage's output (application order of Eq. HA28)
+    f0 = dft2(x, dx, dy)
+    v1 = cm(f0, -params["H"], dwx, dwy)
+    w1 = idft2(v1, dwx, dwy)
+    v2 = cm(w1, params["C2"], dx, dy)
+    f2 = dft2(v2, dx, dy)
+    v3 = cm(f2, -params["Bp"], dwx, dwy)
+    w3 = idft2(v3, dwx, dwy)
+    v4 = cm(w3, params["C1"], dx, dy)
+    # backward
+    g4 = np.asarray(gbar, dtype=np.complex128)
+    g3 = idft2_adj(cm(g4, -params["C1"], dx, dy), dwx, dwy)
+    g2 = dft2_adj(cm(g3, params["Bp"], dwx, dwy), dx, dy)
+    g1 = idft2_adj(cm(g2, -params["C2"], dx, dy), dwx, dwy)
+    gx = dft2_adj(cm(g1, params["H"], dwx, dwy), dx, dy)
+
+    def contrib(g, v, weights):
+        q = np.imag(np.conj(g) * v)
+        return [-float(np.sum(w * q)) for w in weights]
+
+    def magnitude(g, v, weights):
+        q = np.abs(g) * np.abs(v)
+        return [float(np.sum(np.abs(w) * q)) for w in weights]
+
+    stages = [(g1, v1, _phase_weights(nx, ny, dwx, dwy, -1.0)),   # H (CM^{-H} in frequency)
+              (g3, v3, _phase_weights(nx, ny, dwx, dwy, -1.0)),   # B'
+              (g4, v4, _phase_weights(nx, ny, dx, dy, +1.0)),     # C1
+              (g2, v2, _phase_weights(nx, ny, dx, dy, +1.0))]     # C2
+    grad = []
+    for g, v, w in stages:
+        grad += contrib(g, v, w)
+    if with_abs:
+        mag = []
+        for g, v, w in stages:
+            mag += magnitude(g, v, w)
+        return gx, np.array(grad), np.array(mag)
+    return gx, np.array(grad)
+
+
+def loss_and_grad(x, y_target, m, h0, dx, dy):
+    """l = ||forward(x; theta) - y_target||^2 with theta = theta_from_abcd(m) and
+    H = h_of_theta(theta, h0). Returns (l, dl/dRe x + j dl/dIm x, dl/dtheta[10],
+    dl/dchirp[12])."""
+    th = theta_from_abcd(m)
+    params = params_from_theta(th, h0)
+    y = forward(x, params, dx, dy)
+    r = y - y_target
+    loss = float(np.sum(np.abs(r) ** 2))
+    gx, gch = chain_vjp(x, 2.0 * r, params, dx, dy)
+    gth = chirp_jacobian(th, h0).T @ gch
+    return loss, gx, gth, gch

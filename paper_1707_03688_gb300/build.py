@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(PKG, "libnslct.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC] + ARCH
+# extra nvcc flags (e.g. -DNSLCT_E_LARGE=16 to build the radix-16 variant of the 2048/4096 kernels)
+EXTRA = os.environ.get("NSLCT_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:
@@ -34,8 +36,7 @@ def _units():
     units = []
     for real, tag in (("float", "f32"), ("double", "f64")):
         for g in range(4):
-            defs = [f"-DNSLCT_REAL={real}", f"-DNSLCT_GROUP={g}",
-                    f"-DNSLCT_LAUNCH_FN=launch_{tag}_g{g}", f"-DNSLCT_PREPARE_FN=prepare_{tag}_g{g}"]
+            defs = [f"-DNSLCT_REAL={real}", f"-DNSLCT_GROUP={g}", f"-DNSLCT_SUFFIX={tag}_g{g}"]
             units.append(("passes.cu", f"passes_{tag}_g{g}.o", defs))
     for src in sorted(os.listdir(CSRC)):
         if src == "passes.cu":
@@ -47,6 +48,13 @@ def _units():
 
 def _deps_mtime() -> float:
     newest = 0.0
+    stamp = os.path.join(BUILD_DIR, "flags.txt")
+    flags = " ".join(EXTRA)
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        os.makedirs(BUILD_DIR, exist_ok=True)
+        with open(stamp, "w") as f:
+            f.write(flags)
+    newest = max(newest, os.path.getmtime(stamp))
     for d in (CSRC, INCLUDE):
         for name in os.listdir(d):
             newest = max(newest, os.path.getmtime(os.path.join(d, name)))
@@ -66,7 +74,7 @@ def build(verbose: bool = False, jobs: int | None = None, force: bool = False) -
         obj_path = os.path.join(BUILD_DIR, obj)
         if not force and os.path.exists(obj_path) and os.path.getmtime(obj_path) >= deps:
             return obj_path, None
-        cmd = [nvcc] + COMMON + extra + ["-x", "cu", "-c", os.path.join(CSRC, src), "-o", obj_path]
+        cmd = [nvcc] + COMMON + EXTRA + extra + ["-x", "cu", "-c", os.path.join(CSRC, src), "-o", obj_path]
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "fft_schedule.h"
+#include "grad_math.h"
 #include "plan_math.h"
 
 using namespace nslct;
@@ -30,13 +31,16 @@ struct DeviceGuard {
 
 // Per-stage twiddle table of length L (layout in fft_schedule.h): for stage
 // st >= 1 with radix RD and NS earlier points, entry [jm][r] = W_{NS RD}^{jm r}.
+// Per-stage twiddle table of length L for kernels holding E elements per
+// thread (layout in fft_schedule.h): for stage st >= 1 with radix RD and NS
+// earlier points, entry [jm][r] = W_{NS RD}^{jm r}.
 template <typename R>
-int upload_twiddles(int L, void** dev) {
+int upload_twiddles(int L, int E, void** dev) {
   struct C2 { R x, y; };
-  const int n = twiddle_table_size(L) > 0 ? twiddle_table_size(L) : 1;
+  const int n = twiddle_table_size(L, E) > 0 ? twiddle_table_size(L, E) : 1;
   std::vector<C2> host(n, C2{(R)1, (R)0});
-  for (int st = 1; st < num_stages(L); ++st) {
-    const int rd = stage_radix(L, st), ns = stage_ns(L, st), off = stage_table_offset(L, st);
+  for (int st = 1; st < num_stages(L, E); ++st) {
+    const int rd = stage_radix(L, E, st), ns = stage_ns(L, E, st), off = stage_table_offset(L, E, st);
     for (int jm = 0; jm < ns; ++jm)
       for (int r = 0; r < rd; ++r) {
         const long num = (long)jm * r, den = (long)ns * rd;
@@ -56,6 +60,9 @@ int upload_twiddles(int L, void** dev) {
 
 void free_plan(nslct_plan_s* p) {
   if (!p) return;
+  if (p->ws) cudaFree(p->ws);
+  if (p->err) cudaFree(p->err);
+  if (p->partials) cudaFree(p->partials);
   if (p->tw_y && p->tw_y != p->tw_x) cudaFree(p->tw_y);
   if (p->tw_x) cudaFree(p->tw_x);
   delete p;
@@ -74,14 +81,31 @@ int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, 
   DeviceGuard g(p->device);
   if (!g.ok) return NSLCT_E_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  PassDesc d[5];
+  build_chain_descs(p, in, out, inverse, d);
+  for (int k = first; k <= last; ++k) {
+    const int rc = launch(p, chain_pass_is_column(k), d[k], s);
+    if (rc != NSLCT_OK) return rc;
+  }
+  return NSLCT_OK;
+}
+
+}  // namespace
+
+namespace nslct {
+
+bool chain_pass_is_column(int k) { return k == 1 || k == 3; }
+
+// The five passes of the forward chain (Eq. HA28, right to left) or of the
+// inverse chain (Eq. CCCMCCCM04) from `in` (row-major) to `out` (row-major),
+// with `out` holding the tiled intermediate field between passes.
+void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool inverse, PassDesc d[5]) {
   const double ccs = -1.0 / ((double)p->Nx * (double)p->Ny);  // each CC's constant, Eq. BasicDFT16/20
   PassDesc base{};
   base.Nx = p->Nx;
   base.Ny = p->Ny;
   base.scale = 1.0;
-
-  PassDesc d[5];
-  for (auto& x : d) x = base;
+  for (int k = 0; k < 5; ++k) d[k] = base;
   // pass 1: row pass, caller layout -> tiled layout in `out`
   d[0].in = in; d[0].out = out; d[0].in_tiled = 0; d[0].out_tiled = 1; d[0].tw = p->tw_y;
   // passes 2..4 in place on the tiled field; pass 5 back to the caller layout
@@ -95,35 +119,27 @@ int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, 
   d[3].t1 = kFwd; d[3].t2 = kInv;
   d[4].t1 = kInv; d[4].scale = ccs;
   if (!inverse) {
-    // CC^H, CM^{C2}, CC^{B'}, CM^{C1}  (Eq. HA28, right to left)
+    // CC^H, CM^{C2}, CC^{B'}, CM^{C1}
     d[0].t1 = kFwd;
     d[1].chirp = p->fwd_chi_h;
     d[2].chirp = p->fwd_cm_c2;
     d[3].chirp = p->fwd_chi_bp;
     d[4].has_chirp = 1; d[4].chirp = p->fwd_cm_c1;
   } else {
-    // CM^{-C1}, CC^{-B'}, CM^{-C2}, CC^{-H}  (Eq. CCCMCCCM04, right to left)
+    // CM^{-C1}, CC^{-B'}, CM^{-C2}, CC^{-H}
     d[0].has_chirp = 1; d[0].chirp = p->inv_cm_c1; d[0].t2 = kFwd;
     d[1].chirp = p->inv_chi_bp;
     d[2].chirp = p->inv_cm_c2;
     d[3].chirp = p->inv_chi_h;
   }
-  for (auto& x : d) {
-    x.fscale = (float)x.scale;
-    x.scale_only = (!x.has_chirp && x.scale != 1.0) ? 1 : 0;
-    x.num_sms = p->num_sms;
+  for (int k = 0; k < 5; ++k) {
+    d[k].fscale = (float)d[k].scale;
+    d[k].scale_only = (!d[k].has_chirp && d[k].scale != 1.0) ? 1 : 0;
+    d[k].num_sms = p->num_sms;
+    d[k].err = p->err;
   }
-  const bool cols[5] = {false, true, false, true, false};
-  for (int k = first; k <= last; ++k) {
-    const int rc = launch(p, cols[k], d[k], s);
-    if (rc != NSLCT_OK) return rc;
-  }
-  return NSLCT_OK;
 }
 
-}  // namespace
-
-namespace nslct {
 bool supported_length(int L) {
   switch (L) {
     case 8: case 16: case 32: case 64: case 128: case 256: case 512: case 1024: case 2048: case 4096:
@@ -202,16 +218,23 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
     dst[k][0] = src[k]->m00; dst[k][1] = src[k]->m01; dst[k][2] = src[k]->m10; dst[k][3] = src[k]->m11;
   }
   fill_chirps(p);
+  p->has_theta = theta_from_abcd(p->M, p->theta) ? 1 : 0;
+  if (p->has_theta) chirp_jacobian(p->theta, p->H, p->jac);
 
   if (cudaGetDevice(&p->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
     free_plan(p);
     return NSLCT_E_CUDA;
   }
-  rc = p->prec ? upload_twiddles<double>(Nx, &p->tw_x) : upload_twiddles<float>(Nx, &p->tw_x);
+  if (cudaMalloc(&p->err, sizeof(unsigned int)) != cudaSuccess) { p->err = nullptr; free_plan(p); return NSLCT_E_NOMEM; }
+  if (cudaMemset(p->err, 0, sizeof(unsigned int)) != cudaSuccess) { free_plan(p); return NSLCT_E_CUDA; }
+  const bool f32 = p->prec == 0;
+  rc = f32 ? upload_twiddles<float>(Nx, kernel_elems(Nx, true), &p->tw_x)
+           : upload_twiddles<double>(Nx, kernel_elems(Nx, false), &p->tw_x);
   if (rc == NSLCT_OK) {
     if (Ny == Nx) p->tw_y = p->tw_x;
-    else rc = p->prec ? upload_twiddles<double>(Ny, &p->tw_y) : upload_twiddles<float>(Ny, &p->tw_y);
+    else rc = f32 ? upload_twiddles<float>(Ny, kernel_elems(Ny, true), &p->tw_y)
+                  : upload_twiddles<double>(Ny, kernel_elems(Ny, false), &p->tw_y);
   }
   if (rc == NSLCT_OK) rc = p->prec ? prepare_pass_f64(Nx) : prepare_pass_f32(Nx);
   if (rc == NSLCT_OK && Ny != Nx) rc = p->prec ? prepare_pass_f64(Ny) : prepare_pass_f32(Ny);
@@ -234,6 +257,33 @@ int nslct_derive(const double abcd[16], unsigned flags, const double* h_user, do
   }
   if (abcd_used) std::memcpy(abcd_used, m, sizeof(m));
   if (objective) *objective = ha_objective(m, dc.H);
+  return NSLCT_OK;
+}
+
+int nslct_plan_theta(nslct_plan_t* out, const double theta[10], const double h0[4], int Nx, int Ny, double dx,
+                     double dy, unsigned flags) {
+  if (!out) return NSLCT_E_ARG;
+  *out = nullptr;
+  if (!theta) return NSLCT_E_ARG;
+  for (int i = 0; i < 10; ++i)
+    if (!std::isfinite(theta[i])) return NSLCT_E_ARG;
+  const double det_l = theta[3] * theta[6] - theta[4] * theta[5];
+  if (!(std::fabs(det_l) > 1e-12)) return NSLCT_E_ARG;
+  double m[16];
+  abcd_from_theta(theta, m);
+  flags &= ~(unsigned)(NSLCT_H_MASK | NSLCT_PROJECT_SP4);
+  if (!h0) return nslct_plan_ex(out, m, Nx, Ny, dx, dy, flags, nullptr);
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(h0[i])) return NSLCT_E_ARG;
+  double h[4];
+  h_of_theta(theta, h0, h);
+  return nslct_plan_ex(out, m, Nx, Ny, dx, dy, flags | NSLCT_H_USER, h);
+}
+
+int nslct_plan_theta_get(nslct_plan_t p, double theta[10]) {
+  if (!p || !theta) return NSLCT_E_ARG;
+  if (!p->has_theta) return NSLCT_E_UNSUPPORTED;
+  std::memcpy(theta, p->theta, sizeof(p->theta));
   return NSLCT_OK;
 }
 
@@ -271,6 +321,20 @@ int nslct_inverse(nslct_plan_t p, const void* in, void* out, nslct_stream_t stre
 int nslct_forward_pass(nslct_plan_t p, int pass, const void* in, void* out, nslct_stream_t stream) {
   if (pass < 0 || pass > 4) return NSLCT_E_ARG;
   return run_chain(p, in, out, stream, false, pass, pass);
+}
+
+int nslct_status(nslct_plan_t p) {
+  if (!p) return NSLCT_E_ARG;
+  DeviceGuard g(p->device);
+  if (!g.ok) return NSLCT_E_CUDA;
+  unsigned int word = 0;
+  if (cudaMemcpy(&word, p->err, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess) return NSLCT_E_CUDA;
+  if (word) {
+    const unsigned int zero = 0;
+    cudaMemcpy(p->err, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    return NSLCT_E_TIMEOUT;
+  }
+  return NSLCT_OK;
 }
 
 int nslct_destroy(nslct_plan_t p) {

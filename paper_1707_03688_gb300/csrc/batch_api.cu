@@ -1,0 +1,194 @@
+// Batched NsDLCT over fields of uneven sizes, each with its own ABCD matrix:
+// nslct_plan_batch / nslct_batch_* (see include/nslct.h).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "batch_common.h"
+
+using namespace nslct;
+
+struct nslct_batch_s {
+  int n = 0;
+  int device = 0;
+  int num_sms = 0;
+  std::vector<nslct_plan_t> plans;
+  PassDesc* d_descs = nullptr;      // [5][n]
+  BatchItem* d_items = nullptr;     // all passes' work lists back to back
+  int item_off[5] = {0};
+  int nitems[5] = {0};
+  int* d_counters = nullptr;        // one per pass
+  bool bound = false;
+  std::vector<const void*> in;
+  std::vector<void*> out;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+
+void free_batch(nslct_batch_s* b) {
+  if (!b) return;
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_descs) cudaFree(b->d_descs);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_counters) cudaFree(b->d_counters);
+  for (auto p : b->plans) nslct_destroy(p);
+  delete b;
+}
+
+int enqueue(nslct_batch_s* b, cudaStream_t s) {
+  if (cudaMemsetAsync(b->d_counters, 0, 5 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
+  for (int k = 0; k < 5; ++k) {
+    if (b->nitems[k] == 0) continue;
+    const int grid = std::min(b->nitems[k], b->num_sms);
+    const PassDesc* descs = b->d_descs + (size_t)k * b->n;
+    const BatchItem* items = b->d_items + b->item_off[k];
+    const int rc = chain_pass_is_column(k) ? launch_batch_col(grid, descs, items, b->nitems[k], b->d_counters + k, s)
+                                           : launch_batch_row(grid, descs, items, b->nitems[k], b->d_counters + k, s);
+    if (rc != NSLCT_OK) return rc;
+  }
+  return NSLCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const int* Nx, const int* Ny,
+                     const double* dx, const double* dy, unsigned flags) {
+  if (!out) return NSLCT_E_ARG;
+  *out = nullptr;
+  if (nfields <= 0 || !abcd || !Nx || !Ny || !dx || !dy) return NSLCT_E_ARG;
+  if ((flags & NSLCT_PREC_MASK) != NSLCT_PREC_FP32) return NSLCT_E_UNSUPPORTED;
+  for (int f = 0; f < nfields; ++f)
+    if (batch_panel_lines(Nx[f]) == 0 || batch_panel_lines(Ny[f]) == 0) return NSLCT_E_SIZE;
+  nslct_batch_s* b = new (std::nothrow) nslct_batch_s();
+  if (!b) return NSLCT_E_NOMEM;
+  b->n = nfields;
+  if (cudaGetDevice(&b->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+    free_batch(b);
+    return NSLCT_E_CUDA;
+  }
+  for (int f = 0; f < nfields; ++f) {
+    nslct_plan_t p = nullptr;
+    const int rc = nslct_plan(&p, abcd + 16 * (size_t)f, Nx[f], Ny[f], dx[f], dy[f], flags);
+    if (rc != NSLCT_OK) { free_batch(b); return rc; }
+    b->plans.push_back(p);
+  }
+  // work lists: per pass, every field's panels, longest lines first
+  std::vector<BatchItem> all;
+  for (int k = 0; k < 5; ++k) {
+    const bool col = chain_pass_is_column(k);
+    std::vector<int> order(nfields);
+    for (int f = 0; f < nfields; ++f) order[f] = f;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      const int la = col ? Nx[a] : Ny[a], lc = col ? Nx[c] : Ny[c];
+      return la > lc;
+    });
+    b->item_off[k] = (int)all.size();
+    for (int f : order) {
+      const int L = col ? Nx[f] : Ny[f];
+      const int lines = col ? Ny[f] : Nx[f];
+      const int P = batch_panel_lines(L);
+      for (int panel = 0; panel * P < lines; ++panel) all.push_back(BatchItem{f, panel});
+    }
+    b->nitems[k] = (int)all.size() - b->item_off[k];
+  }
+  if (cudaMalloc(&b->d_items, all.size() * sizeof(BatchItem)) != cudaSuccess ||
+      cudaMalloc(&b->d_descs, 5 * (size_t)nfields * sizeof(PassDesc)) != cudaSuccess ||
+      cudaMalloc(&b->d_counters, 5 * sizeof(int)) != cudaSuccess) {
+    free_batch(b);
+    return NSLCT_E_NOMEM;
+  }
+  if (cudaMemcpy(b->d_items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+      prepare_batch_row() != NSLCT_OK || prepare_batch_col() != NSLCT_OK) {
+    free_batch(b);
+    return NSLCT_E_CUDA;
+  }
+  *out = b;
+  return NSLCT_OK;
+}
+
+int nslct_batch_size(nslct_batch_t b) { return b ? b->n : 0; }
+
+int nslct_batch_plan(nslct_batch_t b, int field, nslct_plan_t* plan) {
+  if (!b || !plan || field < 0 || field >= b->n) return NSLCT_E_ARG;
+  *plan = b->plans[field];
+  return NSLCT_OK;
+}
+
+int nslct_batch_bind(nslct_batch_t b, const void* const* in, void* const* out) {
+  if (!b || !in || !out) return NSLCT_E_ARG;
+  std::vector<PassDesc> descs(5 * (size_t)b->n);
+  for (int f = 0; f < b->n; ++f) {
+    if (!in[f] || !out[f]) return NSLCT_E_ARG;
+    if ((reinterpret_cast<uintptr_t>(in[f]) | reinterpret_cast<uintptr_t>(out[f])) & 15u) return NSLCT_E_ARG;
+    PassDesc d[5];
+    build_chain_descs(b->plans[f], in[f], out[f], false, d);
+    for (int k = 0; k < 5; ++k) descs[(size_t)k * b->n + f] = d[k];
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != b->device) cudaSetDevice(b->device);
+  const bool ok = cudaMemcpy(b->d_descs, descs.data(), descs.size() * sizeof(PassDesc), cudaMemcpyHostToDevice) ==
+                  cudaSuccess;
+  if (prev != b->device) cudaSetDevice(prev);
+  if (!ok) return NSLCT_E_CUDA;
+  b->in.assign(in, in + b->n);
+  b->out.assign(out, out + b->n);
+  b->bound = true;
+  if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  return NSLCT_OK;
+}
+
+int nslct_batch_capture(nslct_batch_t b, nslct_stream_t stream) {
+  if (!b || !b->bound) return NSLCT_E_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!s) return NSLCT_E_ARG;  // the legacy default stream cannot be captured
+  if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NSLCT_E_CUDA;
+  const int rc = enqueue(b, s);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc != NSLCT_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != NSLCT_OK ? rc : NSLCT_E_CUDA;
+  }
+  if (cudaGraphInstantiate(&b->graph_exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    b->graph_exec = nullptr;
+    return NSLCT_E_CUDA;
+  }
+  b->graph = g;
+  return NSLCT_OK;
+}
+
+int nslct_batch_forward(nslct_batch_t b, nslct_stream_t stream) {
+  if (!b || !b->bound) return NSLCT_E_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (b->graph_exec) return cudaGraphLaunch(b->graph_exec, s) == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+  return enqueue(b, s);
+}
+
+int nslct_batch_forward_each(nslct_batch_t b, nslct_stream_t stream) {
+  if (!b || !b->bound) return NSLCT_E_ARG;
+  for (int f = 0; f < b->n; ++f) {
+    const int rc = nslct_forward(b->plans[f], b->in[f], b->out[f], stream);
+    if (rc != NSLCT_OK) return rc;
+  }
+  return NSLCT_OK;
+}
+
+int nslct_batch_destroy(nslct_batch_t b) {
+  free_batch(b);
+  return NSLCT_OK;
+}
+
+}  // extern "C"

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -214,19 +215,19 @@ __device__ __forceinline__ void load_twiddles(const cpx<R>* __restrict__ row, cp
   }
 }
 
-template <typename R, int L, int P>
+template <typename R, int L, int P, int E_ = elems_per_thread(L)>
 struct LineFft {
-  static constexpr int E = elems_per_thread(L);
+  static constexpr int E = E_;
   static constexpr int T_LINE = L / E;
-  static constexpr int S = num_stages(L);
+  static constexpr int S = num_stages(L, E);
   static_assert(L % E == 0, "bad E");
 
   // One Stockham stage; FIRST stage reads the registers, later stages read the
   // shared-memory line; the LAST stage leaves its result in registers.
   template <int ST>
   static __device__ __forceinline__ void stage(cpx<R>* v, cpx<R>* sm, int t, int p, const cpx<R>* __restrict__ tw) {
-    constexpr int RD = stage_radix(L, ST);
-    constexpr int NS = stage_ns(L, ST);
+    constexpr int RD = stage_radix(L, E, ST);
+    constexpr int NS = stage_ns(L, E, ST);
     constexpr bool FIRST = (ST == 0);
     constexpr bool LAST = (ST == S - 1);
     constexpr int NB = E / RD;  // butterflies per thread
@@ -246,7 +247,7 @@ struct LineFft {
       const int jm = j % NS;
       if constexpr (NS > 1) {
         cpx<R> w[RD];
-        load_twiddles<R, RD>(tw + stage_table_offset(L, ST) + jm * RD, w);
+        load_twiddles<R, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
 #pragma unroll
         for (int r = 1; r < RD; ++r) x[r] = cmul<R>(x[r], w[r]);
       }
@@ -324,9 +325,8 @@ __device__ __forceinline__ int elem_index(int i, int j, int Ny, int tiled) {
 // after, and e < N/2 exactly when s < E/2 because N/2 is a multiple of
 // T_LINE). So the Q0.64 phase is advanced with two 64-bit additions per
 // element: q(s+1) = q(s) + D(s), D(s+1) = D(s) + 2 k T^2, all exact mod 2^64.
-template <typename R, int L, bool COL>
+template <typename R, int L, bool COL, int E = elems_per_thread(L)>
 __device__ __forceinline__ void apply_chirp(cpx<R>* v, const PassDesc& d, int t, int line, R scale) {
-  constexpr int E = elems_per_thread(L);
   constexpr int T = L / E;
   const int nl = COL ? d.Ny : d.Nx;   // length of the other axis
   // coordinate of the line and of element 0
@@ -429,125 +429,246 @@ pass_kernel(PassDesc d) {
 }
 
 // ---------------------------------------------------------------------------
-// v2 (FP32): persistent CTAs, one per SM. The next panel is copied
-// global -> shared with 16-byte cp.async while the current one is in registers
-// going through the FFTs, so HBM reads overlap the arithmetic.
+// v3 (FP32): persistent CTAs, one per SM, with TMA.
+//   * the NEXT panel streams global -> shared (stg_in) through the Tensor
+//     Memory Accelerator while the current one is in registers going through
+//     the FFTs: a 1D bulk copy per row / row pair for row passes, a 2D tiled
+//     tensor copy (boxes of 2P complex x up to 256 row pairs) for the strided
+//     column panels; completion is tracked by an mbarrier with a transaction
+//     byte count;
+//   * results go registers -> shared (stg_out) -> global by TMA stores, so a
+//     column panel's 32-byte sectors leave as a few bulk operations instead of
+//     thousands of scattered 8-byte stores.
+// Every wait on the mbarrier is bounded: on expiry the CTA sets bit 0 of the
+// plan's device status word (d.err) and leaves; nslct_status reports it.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+// 16-byte asynchronous global -> shared copies (used by the batched kernels)
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(map), "r"(x),
+               "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Bounded wait (one thread) for the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 template <int L, bool COL> struct PShape {
-  static constexpr int E = elems_per_thread(L);
+  static constexpr int E = kernel_elems(L, true);
   static constexpr int T_LINE = L / E;
-  static constexpr int P0 = 512 / T_LINE;
+  // panel of ~8192 complex per CTA (~4096 for 24-element threads) keeps the
+  // exchange buffer and the two staging buffers within 227 KB of shared memory
+  static constexpr int MAXT = E > 16 ? 256 : (E < 16 ? 1024 : 512);
+  static constexpr int P0 = MAXT / T_LINE;
   static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);
   static constexpr int THREADS = T_LINE * P;
   static constexpr int XSM = P * (L + L / 16);                   // exchange buffer entries
-  static constexpr int STG = COL ? P * L : P * (L + 8);          // staging buffer entries (row-major rows padded)
-  static constexpr size_t SMEM = (size_t)(XSM + STG) * sizeof(float2);
+  static constexpr int STG = COL ? P * L : P * (L + 8);          // one staging buffer (row-major rows padded)
+  // column panels leave through an output staging buffer and TMA stores; row
+  // panels are whole contiguous rows and are stored straight from registers
+  static constexpr int NSTG = COL ? 2 : 1;
+  static constexpr size_t SMEM = (size_t)(XSM + NSTG * STG) * sizeof(float2) + 16;
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+  // TMA boxes start on 128-byte boundaries of shared memory
+  static_assert((XSM * sizeof(float2)) % 128 == 0 && (STG * sizeof(float2)) % 128 == 0, "staging alignment");
 };
+
+// Row pairs per TMA box of a column panel: all of them up to 256, else a
+// divisor of the row-pair count (every supported Nx/2 above 256 is a multiple
+// of 128), so the boxes tile the panel exactly.
+__host__ __device__ __forceinline__ int col_box_rows(int rows) {
+  return rows <= 256 ? rows : (rows % 256 == 0 ? 256 : 128);
+}
 
 // staging index of element e of panel line p
 template <int L, bool COL, int P>
-__device__ __forceinline__ int stg_index(int p, int e, int in_tiled) {
+__device__ __forceinline__ int stg_index(int p, int e, int tiled) {
   if (COL) return (e >> 1) * (2 * P) + (p >> 1) * 4 + (e & 1) * 2 + (p & 1);
-  if (in_tiled) return (p >> 1) * (2 * L) + (e >> 1) * 4 + (p & 1) * 2 + (e & 1);
+  if (tiled) return (p >> 1) * (2 * L) + (e >> 1) * 4 + (p & 1) * 2 + (e & 1);
   return p * (L + 8) + e;
 }
 
-// Issue the 16-byte copies of one panel into the staging buffer.
+// Thread 0: start the copies of one panel into `stg`, arming the mbarrier.
 template <int L, bool COL>
-__device__ __forceinline__ void stage_panel(float2* stg, const float2* __restrict__ in, const PassDesc& d, int panel) {
-  using Sh = PShape<L, COL>;
-  constexpr int P = Sh::P;
-  constexpr int CHUNKS = P * L / 2;  // 16-byte chunks per panel
+__device__ __forceinline__ void tma_load_panel(float2* stg, const float2* in, const CUtensorMap* map,
+                                               const PassDesc& d, int panel, uint64_t* bar) {
+  constexpr int P = PShape<L, COL>::P;
   const int first = panel * P;
   if (COL) {
-    // row pair a: P/2 tiles (2P complex, P chunks) starting at tile first/2
-    const int tiles_valid = min(P, d.Ny - first) / 2;
-    for (int c = threadIdx.x; c < CHUNKS; c += Sh::THREADS) {
-      const int a = c / P, k = c % P;
-      if ((k >> 1) < tiles_valid)
-        cp_async16(stg + a * (2 * P) + k * 2, in + a * (2 * d.Ny) + (first >> 1) * 4 + k * 2);
-    }
-  } else if (d.in_tiled) {
-    // P/2 row pairs, each 2L complex contiguous (L chunks)
-    const int rows_valid = min(P, d.Nx - first);
-    for (int c = threadIdx.x; c < CHUNKS; c += Sh::THREADS) {
-      const int q = c / L, k = c % L;
-      if (2 * q < rows_valid) cp_async16(stg + q * (2 * L) + k * 2, in + ((first >> 1) + q) * (2 * L) + k * 2);
-    }
+    const int rows = d.Nx >> 1;                      // row pairs
+    const int box = col_box_rows(rows);
+    mbar_arrive_expect_tx(bar, (uint32_t)(rows * 2 * P * sizeof(float2)));
+    for (int y0 = 0; y0 < rows; y0 += box) tma_load_2d(stg + y0 * (2 * P), map, 2 * first, y0, bar);
   } else {
-    constexpr int CPR = L / 2;  // chunks per row
-    const int rows_valid = min(P, d.Nx - first);
-    for (int c = threadIdx.x; c < CHUNKS; c += Sh::THREADS) {
-      const int p = c / CPR, k = c % CPR;
-      if (p < rows_valid) cp_async16(stg + p * (L + 8) + k * 2, in + (first + p) * L + k * 2);
+    const int valid = min(P, d.Nx - first);
+    if (d.in_tiled) {
+      mbar_arrive_expect_tx(bar, (uint32_t)((valid >> 1) * 2 * L * sizeof(float2)));
+      for (int q = 0; q < (valid >> 1); ++q)
+        bulk_load(stg + q * (2 * L), in + (size_t)((first >> 1) + q) * (2 * L), 2 * L * sizeof(float2), bar);
+    } else {
+      mbar_arrive_expect_tx(bar, (uint32_t)(valid * L * sizeof(float2)));
+      for (int q = 0; q < valid; ++q) bulk_load(stg + q * (L + 8), in + (size_t)(first + q) * L, L * sizeof(float2), bar);
     }
   }
-  cp_async_commit();
+}
+
+// Thread 0: send one finished panel from `stg` to global memory.
+template <int L, bool COL>
+__device__ __forceinline__ void tma_store_panel(const float2* stg, float2* out, const CUtensorMap* map,
+                                                const PassDesc& d, int panel) {
+  constexpr int P = PShape<L, COL>::P;
+  const int first = panel * P;
+  if (COL) {
+    const int rows = d.Nx >> 1;
+    const int box = col_box_rows(rows);
+    for (int y0 = 0; y0 < rows; y0 += box) tma_store_2d(map, 2 * first, y0, stg + y0 * (2 * P));
+  } else {
+    const int valid = min(P, d.Nx - first);
+    if (d.out_tiled) {
+      for (int q = 0; q < (valid >> 1); ++q)
+        bulk_store(out + (size_t)((first >> 1) + q) * (2 * L), stg + q * (2 * L), 2 * L * sizeof(float2));
+    } else {
+      for (int q = 0; q < valid; ++q) bulk_store(out + (size_t)(first + q) * L, stg + q * (L + 8), L * sizeof(float2));
+    }
+  }
+  bulk_commit();
 }
 
 template <int L, bool COL>
 __global__ void __launch_bounds__(PShape<L, COL>::THREADS, 1)
-pass_kernel_v2(PassDesc d) {
+pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out) {
   using Sh = PShape<L, COL>;
   constexpr int E = Sh::E;
   constexpr int T_LINE = Sh::T_LINE;
   constexpr int P = Sh::P;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* xs = reinterpret_cast<float2*>(smem_raw);
-  float2* stg = xs + Sh::XSM;
+  float2* stg_in = xs + Sh::XSM;
+  float2* stg_out = stg_in + Sh::STG;  // only for column passes
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stg_in + Sh::NSTG * Sh::STG);
+  volatile int& s_ok = *reinterpret_cast<volatile int*>(bar + 1);
 
   const int tid = threadIdx.x;
   const int p = tid % P;
   const int t = tid / P;
   const int nlines = COL ? d.Ny : d.Nx;
   const int npanels = (nlines + P - 1) / P;
-  const float2* __restrict__ in = reinterpret_cast<const float2*>(d.in);
+  const float2* in = reinterpret_cast<const float2*>(d.in);
   float2* out = reinterpret_cast<float2*>(d.out);
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   const float scale = d.fscale;
 
   int panel = blockIdx.x;
-  if (panel < npanels) stage_panel<L, COL>(stg, in, d, panel);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    if (panel < npanels) tma_load_panel<L, COL>(stg_in, in, &map_in, d, panel, bar);
+  }
+  __syncthreads();
+  uint32_t parity = 0;
   for (; panel < npanels; panel += gridDim.x) {
     const int line = panel * P + p;
     const bool valid = line < nlines;
-    cp_async_wait_all();
+    if (tid == 0) {
+      s_ok = mbar_wait_bounded(bar, parity) ? 1 : 0;
+      if (COL) bulk_wait_read_all();  // the previous panel's stores have left stg_out
+    }
     __syncthreads();
+    if (!s_ok) {
+      if (tid == 0) {
+        if (d.err) atomicOr(d.err, 1u);
+        mbar_wait_bounded(bar, parity);  // give the copy in flight one more bounded chance
+        bulk_wait_all();
+      }
+      return;
+    }
+    parity ^= 1u;
     float2 v[E];
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = stg[stg_index<L, COL, P>(p, t + T_LINE * s, d.in_tiled)];
-    __syncthreads();  // staging buffer free again
+    for (int s = 0; s < E; ++s) v[s] = stg_in[stg_index<L, COL, P>(p, t + T_LINE * s, d.in_tiled)];
+    __syncthreads();  // stg_in consumed
     const int next = panel + gridDim.x;
-    if (next < npanels) stage_panel<L, COL>(stg, in, d, next);
+    if (tid == 0 && next < npanels) {
+      fence_proxy_async();
+      tma_load_panel<L, COL>(stg_in, in, &map_in, d, next, bar);
+    }
 
-    if (d.t1 != kNone) LineFft<float, L, P>::run(v, xs, t, p, tw, d.t1 == kInv);
+    if (d.t1 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t1 == kInv);
     if (d.has_chirp) {
-      apply_chirp<float, L, COL>(v, d, t, line, scale);
+      apply_chirp<float, L, COL, E>(v, d, t, line, scale);
     } else if (d.scale_only) {
 #pragma unroll
       for (int s = 0; s < E; ++s) v[s] = make_float2(v[s].x * scale, v[s].y * scale);
     }
-    if (d.t2 != kNone) LineFft<float, L, P>::run(v, xs, t, p, tw, d.t2 == kInv);
+    if (d.t2 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t2 == kInv);
 
-    if (valid) {
+    if constexpr (COL) {
 #pragma unroll
-      for (int s = 0; s < E; ++s) {
-        const int e = t + T_LINE * s;
-        const int i = COL ? e : line;
-        const int j = COL ? line : e;
-        out[elem_index(i, j, d.Ny, d.out_tiled)] = v[s];
-      }
+      for (int s = 0; s < E; ++s) stg_out[stg_index<L, COL, P>(p, t + T_LINE * s, 1)] = v[s];
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) tma_store_panel<L, COL>(stg_out, out, &map_out, d, panel);
+    } else if (valid) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) out[elem_index(line, t + T_LINE * s, d.Ny, d.out_tiled)] = v[s];
     }
   }
-  cp_async_wait_all();
+  if (COL && tid == 0) bulk_wait_all();
 }
+
+// Host: 2D tensor map of the 2x2-tiled field for column panels: rows are row
+// pairs (2 Ny complex, 16 Ny bytes apart), the box is 2P complex wide (P/2
+// tiles) and up to 256 row pairs tall. Complex64 values are 8-byte elements.
+bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P);
 
 template <typename R, int L, bool COL>
 inline int launch_one(const PassDesc& d, cudaStream_t s) {
@@ -556,7 +677,12 @@ inline int launch_one(const PassDesc& d, cudaStream_t s) {
     using Sh = PShape<L, COL>;
     const int npanels = (nlines + Sh::P - 1) / Sh::P;
     const int blocks = npanels < d.num_sms ? npanels : d.num_sms;
-    pass_kernel_v2<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d);
+    alignas(64) CUtensorMap mi{}, mo{};
+    if (COL) {
+      if (!encode_column_map(&mi, d.in, d.Nx, d.Ny, Sh::P) || !encode_column_map(&mo, d.out, d.Nx, d.Ny, Sh::P))
+        return NSLCT_E_CUDA;
+    }
+    pass_kernel_tma<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, mi, mo);
   } else {
     using Sh = PassShape<R, L>;
     const int blocks = (nlines + Sh::P - 1) / Sh::P;
@@ -569,15 +695,175 @@ template <typename R, int L>
 inline int prepare_one() {
   cudaError_t e1, e2;
   if constexpr (sizeof(R) == 4) {
-    e1 = cudaFuncSetAttribute(pass_kernel_v2<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e1 = cudaFuncSetAttribute(pass_kernel_tma<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PShape<L, false>::SMEM);
-    e2 = cudaFuncSetAttribute(pass_kernel_v2<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e2 = cudaFuncSetAttribute(pass_kernel_tma<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PShape<L, true>::SMEM);
   } else {
     using Sh = PassShape<R, L>;
     e1 = cudaFuncSetAttribute(pass_kernel<R, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
     e2 = cudaFuncSetAttribute(pass_kernel<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
   }
+  return (e1 == cudaSuccess && e2 == cudaSuccess) ? NSLCT_OK : NSLCT_E_CUDA;
+}
+
+}  // namespace nslct
+
+namespace nslct {
+
+// ---------------------------------------------------------------------------
+// Dual passes for the adjoint (nslct_backward). Two fields go through the same
+// pass of the inverse chain: the gradient path g (-> grad_in) and the value
+// path y (-> workspace), which recomputes the forward intermediates by
+// inverting the chain instead of storing them. At the pass's chirp point,
+// before the chirp, the CTA accumulates
+//     S_aa = sum a^2 q,  S_ab = sum a b q,  S_bb = sum b^2 q,  q = Im(conj(g) y)
+// with (a, b) the chirp's integer coordinates along (x, y); the host turns
+// these into d loss / d chirp entries. One panel per CTA; partial sums per CTA
+// go to `partials[blockIdx.x][3]` (FP64), reduced later in a fixed order.
+// ---------------------------------------------------------------------------
+template <typename R, int L> struct DualShape {
+  static constexpr int E = kernel_elems(L, sizeof(R) == 4);  // must match the plan's twiddle table
+  static constexpr int T_LINE = L / E;
+  static constexpr int P0 = 512 / T_LINE;
+  static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);
+  static constexpr int THREADS = T_LINE * P;
+  static constexpr int XSM = P * (L + L / 16);
+  static constexpr size_t SMEM = (size_t)XSM * sizeof(cpx<R>) + 32 * 3 * sizeof(double);
+};
+
+template <typename R, int L, bool COL>
+__global__ void __launch_bounds__(DualShape<R, L>::THREADS, 1)
+dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, int accumulate) {
+  using Sh = DualShape<R, L>;
+  constexpr int E = Sh::E;
+  constexpr int T_LINE = Sh::T_LINE;
+  constexpr int P = Sh::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
+  double* red = reinterpret_cast<double*>(smem_raw + (size_t)Sh::XSM * sizeof(cpx<R>));
+
+  const int tid = threadIdx.x;
+  const int p = tid % P;
+  const int t = tid / P;
+  const int nlines = COL ? d.Ny : d.Nx;
+  const int line = blockIdx.x * P + p;
+  const bool valid = line < nlines;
+  const cpx<R>* __restrict__ gin = reinterpret_cast<const cpx<R>*>(d.in);
+  const cpx<R>* __restrict__ yin = reinterpret_cast<const cpx<R>*>(in_y);
+  cpx<R>* gout = reinterpret_cast<cpx<R>*>(d.out);
+  cpx<R>* yout = reinterpret_cast<cpx<R>*>(out_y);
+  const cpx<R>* __restrict__ tw = reinterpret_cast<const cpx<R>*>(d.tw);
+
+  cpx<R> vg[E], vy[E];
+#pragma unroll
+  for (int s = 0; s < E; ++s) {
+    const int e = t + T_LINE * s;
+    const int i = COL ? e : line;
+    const int j = COL ? line : e;
+    const int k = elem_index(i, j, d.Ny, d.in_tiled);
+    vg[s] = valid ? gin[k] : mk<R>((R)0, (R)0);
+    vy[s] = valid ? yin[k] : mk<R>((R)0, (R)0);
+  }
+  if (d.t1 != kNone) {
+    LineFft<R, L, P, E>::run(vg, sm, t, p, tw, d.t1 == kInv);
+    LineFft<R, L, P, E>::run(vy, sm, t, p, tw, d.t1 == kInv);
+  }
+  if (accumulate) {
+    // coordinates as in apply_chirp
+    const int nl = COL ? d.Ny : d.Nx;
+    const int lc = d.freq_domain ? centred_bin(line, nl) : line - nl / 2;
+    // per-thread sums in the plan's precision; FP32 sums carry their rounding
+    // error along (TwoSum), since the weighted terms cancel heavily
+    R sum[3] = {(R)0, (R)0, (R)0}, err[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const int e = t + T_LINE * s;
+      const int ec = d.freq_domain ? centred_bin(e, L) : e - L / 2;
+      const int a = COL ? ec : lc;   // x coordinate
+      const int b = COL ? lc : ec;   // y coordinate
+      const R q = vg[s].x * vy[s].y - vg[s].y * vy[s].x;
+      const R term[3] = {(R)(a * a) * q, (R)(a * b) * q, (R)(b * b) * q};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if constexpr (sizeof(R) == 4) {
+          const R tsum = sum[k] + term[k];
+          const R bp = tsum - sum[k];
+          err[k] += (sum[k] - (tsum - bp)) + (term[k] - bp);
+          sum[k] = tsum;
+        } else {
+          sum[k] += term[k];
+        }
+      }
+    }
+    double acc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] = valid ? (double)sum[k] + (double)err[k] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    const int warp = tid >> 5, lane = tid & 31;
+    __syncthreads();
+    if (lane == 0)
+      for (int k = 0; k < 3; ++k) red[warp * 3 + k] = acc[k];
+    __syncthreads();
+    if (tid == 0) {
+      double tot[3] = {0.0, 0.0, 0.0};
+      for (int w = 0; w < Sh::THREADS / 32; ++w)
+        for (int k = 0; k < 3; ++k) tot[k] += red[w * 3 + k];
+      for (int k = 0; k < 3; ++k) partials[blockIdx.x * 3 + k] = tot[k];
+    }
+  }
+  if (d.has_chirp) {
+    apply_chirp<R, L, COL, E>(vg, d, t, line, (R)d.scale);
+    apply_chirp<R, L, COL, E>(vy, d, t, line, (R)d.scale);
+  } else if (d.scale != 1.0) {
+    const R scale = (R)d.scale;
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      vg[s] = mk<R>(vg[s].x * scale, vg[s].y * scale);
+      vy[s] = mk<R>(vy[s].x * scale, vy[s].y * scale);
+    }
+  }
+  if (d.t2 != kNone) {
+    LineFft<R, L, P, E>::run(vg, sm, t, p, tw, d.t2 == kInv);
+    LineFft<R, L, P, E>::run(vy, sm, t, p, tw, d.t2 == kInv);
+  }
+  __syncthreads();  // in-place: all loads of the panel happened before any store
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const int e = t + T_LINE * s;
+      const int i = COL ? e : line;
+      const int j = COL ? line : e;
+      const int k = elem_index(i, j, d.Ny, d.out_tiled);
+      gout[k] = vg[s];
+      yout[k] = vy[s];
+    }
+  }
+}
+
+// number of CTAs (and partial-sum rows) a dual pass along this axis uses
+template <typename R, int L>
+inline int dual_blocks(int nlines) { return (nlines + DualShape<R, L>::P - 1) / DualShape<R, L>::P; }
+
+template <typename R, int L, bool COL>
+inline int launch_dual_one(const PassDesc& d, const void* in_y, void* out_y, double* partials, int accumulate,
+                           cudaStream_t s) {
+  using Sh = DualShape<R, L>;
+  const int nlines = COL ? d.Ny : d.Nx;
+  dual_pass_kernel<R, L, COL><<<dual_blocks<R, L>(nlines), Sh::THREADS, Sh::SMEM, s>>>(d, in_y, out_y, partials,
+                                                                                      accumulate);
+  return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+}
+
+template <typename R, int L>
+inline int prepare_dual_one() {
+  using Sh = DualShape<R, L>;
+  cudaError_t e1 = cudaFuncSetAttribute(dual_pass_kernel<R, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Sh::SMEM);
+  cudaError_t e2 = cudaFuncSetAttribute(dual_pass_kernel<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Sh::SMEM);
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? NSLCT_OK : NSLCT_E_CUDA;
 }
 

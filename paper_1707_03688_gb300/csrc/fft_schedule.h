@@ -5,46 +5,57 @@ namespace nslct {
 
 __host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// elements per thread
+// Elements per thread of the FP32 persistent kernels for the largest
+// power-of-two lines (2048, 4096): 8 gives 1024-thread CTAs (radix-8 stages),
+// 16 gives 512-thread CTAs (radix-16 stages). Overridable at build time.
+#ifndef NSLCT_E_LARGE
+#define NSLCT_E_LARGE 16
+#endif
+
+// default elements per thread: 16 for 2^a lines, 24 for 3*2^a lines (capped by L)
 __host__ __device__ constexpr int elems_per_thread(int L) {
   return is_pow2(L) ? (L >= 16 ? 16 : L) : (L >= 24 ? 24 : L);
 }
-// radix of stage `st`: the largest allowed radix first, then powers of two
-__host__ __device__ constexpr int stage_radix(int L, int st) {
+// elements per thread of the kernel that runs length L (FP32 or FP64)
+__host__ __device__ constexpr int kernel_elems(int L, bool f32) {
+  return (f32 && is_pow2(L) && L >= 2048) ? NSLCT_E_LARGE : elems_per_thread(L);
+}
+// largest power of two <= n that divides e
+__host__ __device__ constexpr int pow2_radix(int n, int e) {
+  int r = 1;
+  while (r * 2 <= n && e % (r * 2) == 0) r *= 2;
+  return r;
+}
+// radix of stage `st` when each thread holds E elements: E first, then the
+// largest power of two dividing E that fits the rest
+__host__ __device__ constexpr int stage_radix(int L, int E, int st) {
   int rem = L;
-  int first = is_pow2(L) ? (L >= 16 ? 16 : L) : (L >= 24 ? 24 : L);
-  int r = first;
+  int r = E;
   for (int i = 0; i <= st; ++i) {
-    if (i == 0) {
-      r = first;
-    } else {
-      int big = is_pow2(L) ? 16 : 8;
-      r = rem >= big ? big : rem;
-    }
+    r = (i == 0) ? E : pow2_radix(rem, E);
     if (i < st) rem /= r;
   }
   return r;
 }
-__host__ __device__ constexpr int num_stages(int L) {
+__host__ __device__ constexpr int num_stages(int L, int E) {
   int rem = L, s = 0;
-  while (rem > 1) { rem /= stage_radix(L, s); ++s; }
+  while (rem > 1) { rem /= stage_radix(L, E, s); ++s; }
   return s;
 }
-__host__ __device__ constexpr int stage_ns(int L, int st) {  // product of the radices before `st`
+__host__ __device__ constexpr int stage_ns(int L, int E, int st) {  // product of the radices before `st`
   int ns = 1;
-  for (int i = 0; i < st; ++i) ns *= stage_radix(L, i);
+  for (int i = 0; i < st; ++i) ns *= stage_radix(L, E, i);
   return ns;
 }
-
 
 // Size (in complex entries) of the per-stage twiddle table of length L: for
 // every stage st >= 1 with radix RD and NS = product of the earlier radices,
 // NS * RD entries W_{NS*RD}^{jm*r} laid out [jm][r].
-__host__ __device__ constexpr int stage_table_offset(int L, int st) {
+__host__ __device__ constexpr int stage_table_offset(int L, int E, int st) {
   int off = 0;
-  for (int i = 1; i < st; ++i) off += stage_ns(L, i) * stage_radix(L, i);
+  for (int i = 1; i < st; ++i) off += stage_ns(L, E, i) * stage_radix(L, E, i);
   return off;
 }
-__host__ __device__ constexpr int twiddle_table_size(int L) { return stage_table_offset(L, num_stages(L)); }
+__host__ __device__ constexpr int twiddle_table_size(int L, int E) { return stage_table_offset(L, E, num_stages(L, E)); }
 
 }  // namespace nslct

@@ -6,6 +6,8 @@
 
 #include "nslct.h"
 
+struct nslct_plan_s;
+
 namespace nslct {
 
 // A quadratic chirp phase in turns, stored as Q0.64 fixed point:
@@ -41,6 +43,7 @@ struct PassDesc {
   int scale_only;      // no chirp but scale != 1
   int num_sms;         // persistent-grid size for the FP32 kernels
   const void* tw;      // per-stage twiddle table of the pass axis length (see fft_schedule.h)
+  unsigned int* err;   // device status word: bit 0 = a bounded wait expired
 };
 
 // Enqueue one pass. `col` selects the axis. Returns an NSLCT_* code.
@@ -50,10 +53,26 @@ int launch_pass_f64(bool col, const PassDesc& d, cudaStream_t s);
 int prepare_pass_f32(int L);
 int prepare_pass_f64(int L);
 
+// Dual (adjoint) passes: gradient path d.in -> d.out and value path in_y -> out_y
+// through the same pass; with `accumulate`, per-CTA sums S_aa, S_ab, S_bb go to
+// partials[cta][3]. dual_blocks_* gives the CTA count of such a pass.
+int launch_dual_f32(bool col, const PassDesc& d, const void* in_y, void* out_y, double* partials, int accumulate,
+                    cudaStream_t s);
+int launch_dual_f64(bool col, const PassDesc& d, const void* in_y, void* out_y, double* partials, int accumulate,
+                    cudaStream_t s);
+int dual_blocks_f32(int L, int nlines);
+int dual_blocks_f64(int L, int nlines);
+
+// The five pass descriptors of the forward or inverse chain (see api.cpp).
+void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool inverse, PassDesc d[5]);
+bool chain_pass_is_column(int k);
+
 // True when L is a length the kernels are instantiated for.
 bool supported_length(int L);
 
 }  // namespace nslct
+
+struct nslct_plan_s;
 
 // The opaque plan (one ABCD matrix, one field size).
 struct nslct_plan_s {
@@ -70,6 +89,13 @@ struct nslct_plan_s {
   // Inverse chain chirps: cm_-C1, chi_+B', cm_-C2, chi_+H.
   nslct::Chirp inv_cm_c1, inv_chi_bp, inv_cm_c2, inv_chi_h;
   int num_sms;         // multiprocessors of `device`
+  int has_theta;       // A invertible: theta and its chirp Jacobian are defined
+  double theta[10];    // (c11,c12,c22, l11,l12,l21,l22, b11,b12,b22), see grad_math.cpp
+  double jac[120];     // d(H, B', C1, C2 entries)/d theta, 12 x 10
+  void* ws;            // backward value-path field (made on first use)
+  double* partials;    // backward per-CTA sums (made on first use)
+  int partials_stride; // rows per pass in `partials`
+  unsigned int* err;   // device status word shared by the plan's kernels
   void* tw_x;          // device twiddles for length Nx
   void* tw_y;          // device twiddles for length Ny (may alias tw_x)
 };

@@ -4,9 +4,11 @@
 // supported length 2^a (8..4096) and 3*2^a (12..1536).
 #include "fft_pass.cuh"
 
-#if !defined(NSLCT_REAL) || !defined(NSLCT_GROUP) || !defined(NSLCT_LAUNCH_FN) || !defined(NSLCT_PREPARE_FN)
-#error "compile with -DNSLCT_REAL=float|double -DNSLCT_GROUP=0..3 -DNSLCT_LAUNCH_FN=... -DNSLCT_PREPARE_FN=..."
+#if !defined(NSLCT_REAL) || !defined(NSLCT_GROUP) || !defined(NSLCT_SUFFIX)
+#error "compile with -DNSLCT_REAL=float|double -DNSLCT_GROUP=0..3 -DNSLCT_SUFFIX=f32_g0|..."
 #endif
+#define NSLCT_CAT2(a, b) a##b
+#define NSLCT_CAT(a, b) NSLCT_CAT2(a, b)
 
 #if NSLCT_GROUP == 0
 #define NSLCT_LENGTHS(X) X(4096) X(2048)
@@ -22,7 +24,7 @@
 
 namespace nslct {
 
-int NSLCT_LAUNCH_FN(bool col, const PassDesc& d, cudaStream_t s) {
+int NSLCT_CAT(launch_, NSLCT_SUFFIX)(bool col, const PassDesc& d, cudaStream_t s) {
   const int L = col ? d.Nx : d.Ny;
   switch (L) {
 #define NSLCT_CASE(LL) \
@@ -33,13 +35,40 @@ int NSLCT_LAUNCH_FN(bool col, const PassDesc& d, cudaStream_t s) {
   }
 }
 
-int NSLCT_PREPARE_FN(int L) {
+int NSLCT_CAT(prepare_, NSLCT_SUFFIX)(int L) {
   switch (L) {
 #define NSLCT_CASE(LL) \
-  case LL: return prepare_one<NSLCT_REAL, LL>();
+  case LL: {                                        \
+    const int rc = prepare_one<NSLCT_REAL, LL>();    \
+    return rc != NSLCT_OK ? rc : prepare_dual_one<NSLCT_REAL, LL>(); \
+  }
     NSLCT_LENGTHS(NSLCT_CASE)
 #undef NSLCT_CASE
     default: return NSLCT_E_SIZE;
+  }
+}
+
+int NSLCT_CAT(launch_dual_, NSLCT_SUFFIX)(bool col, const PassDesc& d, const void* in_y, void* out_y,
+                                         double* partials, int accumulate, cudaStream_t s) {
+  const int L = col ? d.Nx : d.Ny;
+  switch (L) {
+#define NSLCT_CASE(LL)                                                                               \
+  case LL:                                                                                           \
+    return col ? launch_dual_one<NSLCT_REAL, LL, true>(d, in_y, out_y, partials, accumulate, s)      \
+               : launch_dual_one<NSLCT_REAL, LL, false>(d, in_y, out_y, partials, accumulate, s);
+    NSLCT_LENGTHS(NSLCT_CASE)
+#undef NSLCT_CASE
+    default: return NSLCT_E_SIZE;
+  }
+}
+
+int NSLCT_CAT(dual_blocks_, NSLCT_SUFFIX)(int L, int nlines) {
+  switch (L) {
+#define NSLCT_CASE(LL) \
+  case LL: return dual_blocks<NSLCT_REAL, LL>(nlines);
+    NSLCT_LENGTHS(NSLCT_CASE)
+#undef NSLCT_CASE
+    default: return -1;
   }
 }
 

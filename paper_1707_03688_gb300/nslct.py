@@ -37,7 +37,11 @@ NSLCT_PREC_FP64 = 0x100
 # every symbol include/nslct.h declares, in declaration order
 EXPORTED = (
     "nslct_plan", "nslct_plan_ex", "nslct_derive", "nslct_plan_params", "nslct_plan_info",
-    "nslct_forward", "nslct_inverse", "nslct_forward_pass", "nslct_destroy", "nslct_strerror", "nslct_version",
+    "nslct_forward", "nslct_inverse", "nslct_forward_pass", "nslct_backward",
+    "nslct_plan_theta",
+    "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
+    "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_forward_each", "nslct_batch_destroy",
+    "nslct_status", "nslct_destroy", "nslct_strerror", "nslct_version",
 )
 
 
@@ -80,6 +84,20 @@ def load(path: str | None = None):
         "nslct_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_forward_pass": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+        "nslct_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+        "nslct_plan_theta": (ctypes.c_int, [ctypes.POINTER(_VP), _PD, _PD, ctypes.c_int, ctypes.c_int, _D, _D,
+                                            ctypes.c_uint]),
+        "nslct_plan_theta_get": (ctypes.c_int, [_VP, _PD]),
+        "nslct_plan_batch": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _PD, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), _PD, _PD, ctypes.c_uint]),
+        "nslct_batch_size": (ctypes.c_int, [_VP]),
+        "nslct_batch_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+        "nslct_batch_bind": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+        "nslct_batch_forward": (ctypes.c_int, [_VP, _VP]),
+        "nslct_batch_capture": (ctypes.c_int, [_VP, _VP]),
+        "nslct_batch_forward_each": (ctypes.c_int, [_VP, _VP]),
+        "nslct_batch_destroy": (ctypes.c_int, [_VP]),
+        "nslct_status": (ctypes.c_int, [_VP]),
         "nslct_destroy": (ctypes.c_int, [_VP]),
         "nslct_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "nslct_version": (ctypes.c_char_p, []),
@@ -210,6 +228,40 @@ def nslct_forward_pass(plan: int, k: int, x, out, stream=None):
     return out
 
 
+def _ptr(t):
+    return _VP(t.data_ptr()) if t is not None else _VP(0)
+
+
+def nslct_backward(plan: int, grad_out, y, grad_in, grad_theta=None, grad_chirp=None, workspace=None, stream=None):
+    """grad_in = L^H grad_out; optional device float64 tensors grad_theta (10) and grad_chirp (12)."""
+    _check(load().nslct_backward(_VP(plan), _ptr(grad_out), _ptr(y), _ptr(grad_in), _ptr(grad_theta),
+                                 _ptr(grad_chirp), _ptr(workspace), _stream_ptr(stream, grad_in.device)),
+           "nslct_backward")
+    return grad_in
+
+
+def nslct_plan_theta(theta, nx: int, ny: int, dx: float, dy: float, h0=None, flags: int = 0) -> int:
+    """Plan for M(theta) with H = h0 moved onto the feasible plane (see include/nslct.h)."""
+    lib = load()
+    t, pt = _dbl(theta, 10)
+    h, ph = (None, None) if h0 is None else _dbl(h0, 4)
+    handle = _VP(0)
+    _check(lib.nslct_plan_theta(ctypes.byref(handle), pt, ph, int(nx), int(ny), float(dx), float(dy),
+                                ctypes.c_uint(flags)), "nslct_plan_theta")
+    return handle.value
+
+
+def nslct_plan_theta_get(plan: int):
+    th, pth = _out(10)
+    _check(load().nslct_plan_theta_get(_VP(plan), pth), "nslct_plan_theta_get")
+    return th
+
+
+def nslct_status(plan: int) -> int:
+    """NSLCT_OK or NSLCT_E_TIMEOUT (a bounded device wait expired since the last call)."""
+    return int(load().nslct_status(_VP(plan)))
+
+
 def nslct_destroy(plan: int):
     _check(load().nslct_destroy(_VP(plan)), "nslct_destroy")
 
@@ -250,6 +302,41 @@ class Plan:
         self.handle = None
         self.handle = nslct_plan(abcd, self.nx, self.ny, self.dx, self.dy, flags, h_user=h)
 
+    @classmethod
+    def from_theta(cls, theta, nx: int, ny: int, h0=None, dx: float | None = None, dy: float | None = None,
+                   precision: str = "fp32"):
+        """Plan for M(theta) (see nslct_plan_theta)."""
+        import torch
+        self = cls.__new__(cls)
+        self.nx, self.ny = int(nx), int(ny)
+        self.dx = float(dx) if dx is not None else math.sqrt(2 * math.pi / self.nx)
+        self.dy = float(dy) if dy is not None else math.sqrt(2 * math.pi / self.ny)
+        flags = NSLCT_PREC_FP64 if precision == "fp64" else NSLCT_PREC_FP32
+        self.dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.device = torch.cuda.current_device()
+        self.flags = flags
+        self.handle = None
+        self.handle = nslct_plan_theta(theta, self.nx, self.ny, self.dx, self.dy, h0=h0, flags=flags)
+        return self
+
+    def theta(self):
+        return nslct_plan_theta_get(self.handle)
+
+    def backward(self, grad_out, y, grad_in=None, want_theta=True, want_chirp=False, workspace=None, stream=None):
+        """Returns (grad_in, grad_theta or None, grad_chirp or None); gradients are device float64 tensors."""
+        import torch
+        _check_field(grad_out, self.nx, self.ny, self.dtype, self.device, "grad_out")
+        _check_field(y, self.nx, self.ny, self.dtype, self.device, "y")
+        if grad_in is None:
+            grad_in = torch.empty_like(grad_out)
+        _check_field(grad_in, self.nx, self.ny, self.dtype, self.device, "grad_in")
+        if workspace is not None:
+            _check_field(workspace, self.nx, self.ny, self.dtype, self.device, "workspace")
+        gth = torch.zeros(10, dtype=torch.float64, device=grad_out.device) if want_theta else None
+        gch = torch.zeros(12, dtype=torch.float64, device=grad_out.device) if want_chirp else None
+        nslct_backward(self.handle, grad_out, y, grad_in, gth, gch, workspace, stream)
+        return grad_in, gth, gch
+
     def params(self):
         return nslct_plan_params(self.handle)
 
@@ -275,6 +362,84 @@ class Plan:
     def close(self):
         if self.handle:
             nslct_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches
+
+
+def nslct_plan_batch(abcds, nx, ny, dx, dy, flags: int = 0) -> int:
+    lib = load()
+    n = len(nx)
+    m, pm = _dbl(np.asarray(abcds, dtype=np.float64).reshape(n, 16), 16 * n)
+    ax = (ctypes.c_int * n)(*[int(v) for v in nx])
+    ay = (ctypes.c_int * n)(*[int(v) for v in ny])
+    ddx, pdx = _dbl(dx, n)
+    ddy, pdy = _dbl(dy, n)
+    handle = _VP(0)
+    _check(lib.nslct_plan_batch(ctypes.byref(handle), n, pm, ax, ay, pdx, pdy, ctypes.c_uint(flags)),
+           "nslct_plan_batch")
+    return handle.value
+
+
+class Batch:
+    """Fields of uneven sizes, each with its own ABCD matrix (FP32)."""
+
+    def __init__(self, abcds, shapes, method_flags: int = 0):
+        self.shapes = [(int(a), int(b)) for a, b in shapes]
+        nx = [a for a, _ in self.shapes]
+        ny = [b for _, b in self.shapes]
+        dx = [math.sqrt(2 * math.pi / a) for a in nx]
+        dy = [math.sqrt(2 * math.pi / b) for b in ny]
+        self.dx, self.dy = dx, dy
+        self.handle = None
+        self.handle = nslct_plan_batch(abcds, nx, ny, dx, dy, method_flags)
+        self._bound = None
+
+    def plan_handle(self, i: int) -> int:
+        h = _VP(0)
+        _check(load().nslct_batch_plan(_VP(self.handle), int(i), ctypes.byref(h)), "nslct_batch_plan")
+        return h.value
+
+    def params(self, i: int):
+        return nslct_plan_params(self.plan_handle(i))
+
+    def info(self, i: int):
+        return nslct_plan_info(self.plan_handle(i))
+
+    def bind(self, ins, outs):
+        import torch
+        n = len(self.shapes)
+        for (nx, ny), a, b in zip(self.shapes, ins, outs):
+            _check_field(a, nx, ny, torch.complex64, None, "input")
+            _check_field(b, nx, ny, torch.complex64, None, "output")
+        pin = (_VP * n)(*[t.data_ptr() for t in ins])
+        pout = (_VP * n)(*[t.data_ptr() for t in outs])
+        _check(load().nslct_batch_bind(_VP(self.handle), pin, pout), "nslct_batch_bind")
+        self._bound = (list(ins), list(outs))
+
+    def capture(self, stream):
+        _check(load().nslct_batch_capture(_VP(self.handle), _stream_ptr(stream, None)), "nslct_batch_capture")
+
+    def forward(self, stream=None):
+        import torch
+        _check(load().nslct_batch_forward(_VP(self.handle), _stream_ptr(stream, torch.cuda.current_device())),
+               "nslct_batch_forward")
+
+    def forward_each(self, stream=None):
+        import torch
+        _check(load().nslct_batch_forward_each(_VP(self.handle), _stream_ptr(stream, torch.cuda.current_device())),
+               "nslct_batch_forward_each")
+
+    def close(self):
+        if self.handle:
+            load().nslct_batch_destroy(_VP(self.handle))
             self.handle = None
 
     def __del__(self):
