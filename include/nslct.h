@@ -204,6 +204,28 @@ int nslct_plan_theta(nslct_plan_t* out, const double theta[10], const double h0[
 /* nslct_plan_theta_get -- theta of the plan's ABCD (NSLCT_E_UNSUPPORTED if A is singular). */
 int nslct_plan_theta_get(nslct_plan_t plan, double theta[10]);
 
+/*
+ * nslct_backward_noalloc -- nslct_backward for callers that cannot allocate
+ * device memory: code recording a CUDA graph (where cudaMalloc is not allowed
+ * inside the capture), code under a caching allocator that must own every
+ * allocation, or code with a fixed memory budget. The paper has no counterpart;
+ * this is an interface variant of nslct_backward.
+ *   grad_out, grad_in, grad_theta, grad_chirp   as in nslct_backward.
+ *   y_inout    the forward output y (device). It doubles as the value-path
+ *              buffer, so on return it holds L^{-1} y, the reconstructed input.
+ * The call makes no allocation of any kind. Its per-CTA partial sums go to a
+ * fixed device array inside the library (4 x 2049 x 3 doubles, about 196 KB,
+ * enough for every supported size; larger would return NSLCT_E_SIZE), which
+ * every GPU that loads the library holds until the process exits. The first
+ * call on a device looks that array's device address up (cudaGetSymbolAddress
+ * with the plan's device current); make that first call before any stream
+ * capture. Each call rewrites all the array entries it reads, so nothing has
+ * to be cleared between calls; but every call shares the one array, so calls
+ * that overlap on the GPU (other streams, other threads, other plans) race.
+ */
+int nslct_backward_noalloc(nslct_plan_t plan, const void* grad_out, void* y_inout, void* grad_in,
+                           double* grad_theta, double* grad_chirp, nslct_stream_t stream);
+
 /* ---- batches of fields with uneven sizes ------------------------------------ */
 typedef struct nslct_batch_s* nslct_batch_t;  /* opaque, owned by the library */
 

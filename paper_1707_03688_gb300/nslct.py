@@ -37,7 +37,7 @@ NSLCT_PREC_FP64 = 0x100
 # every symbol include/nslct.h declares, in declaration order
 EXPORTED = (
     "nslct_plan", "nslct_plan_ex", "nslct_derive", "nslct_plan_params", "nslct_plan_info",
-    "nslct_forward", "nslct_inverse", "nslct_forward_pass", "nslct_backward",
+    "nslct_forward", "nslct_inverse", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_forward_each", "nslct_batch_destroy",
@@ -85,6 +85,7 @@ def load(path: str | None = None):
         "nslct_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_forward_pass": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
         "nslct_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+        "nslct_backward_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "nslct_plan_theta": (ctypes.c_int, [ctypes.POINTER(_VP), _PD, _PD, ctypes.c_int, ctypes.c_int, _D, _D,
                                             ctypes.c_uint]),
         "nslct_plan_theta_get": (ctypes.c_int, [_VP, _PD]),
@@ -237,6 +238,14 @@ def nslct_backward(plan: int, grad_out, y, grad_in, grad_theta=None, grad_chirp=
     _check(load().nslct_backward(_VP(plan), _ptr(grad_out), _ptr(y), _ptr(grad_in), _ptr(grad_theta),
                                  _ptr(grad_chirp), _ptr(workspace), _stream_ptr(stream, grad_in.device)),
            "nslct_backward")
+    return grad_in
+
+
+def nslct_backward_noalloc(plan: int, grad_out, y_inout, grad_in, grad_theta=None, grad_chirp=None, stream=None):
+    """nslct_backward without any allocation; y_inout is overwritten with L^-1 y (see include/nslct.h)."""
+    _check(load().nslct_backward_noalloc(_VP(plan), _ptr(grad_out), _ptr(y_inout), _ptr(grad_in), _ptr(grad_theta),
+                                         _ptr(grad_chirp), _stream_ptr(stream, grad_in.device)),
+           "nslct_backward_noalloc")
     return grad_in
 
 
