@@ -1,0 +1,97 @@
+"""Batched transforms of fields with uneven sizes (one ABCD per field): the
+persistent per-pass launches and their captured CUDA graph against per-field
+launches and against the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import nslct_oracle as O
+from paper_1707_03688_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [64, 96, 128, 192, 256, 384, 512, 768, 1024]
+
+
+@pytest.fixture(scope="module")
+def N():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_03688_gb300 import build as B
+    B.build()
+    from paper_1707_03688_gb300 import nslct
+    nslct.load()
+    return nslct
+
+
+@pytest.fixture(scope="module")
+def batch_case(N):
+    rng = np.random.default_rng(3)
+    shapes = [(int(rng.choice(SIZES)), int(rng.choice(SIZES))) for _ in range(24)]
+    shapes[0] = (64, 1024)   # extremes included
+    shapes[1] = (1024, 64)
+    abcds = [I.random_symplectic_abcd(3000 + k) for k in range(len(shapes))]
+    fields = [I.blob_field(nx, ny, seed=3100 + k, width_range=(2.0, max(3.0, min(nx, ny) / 8)))
+              for k, (nx, ny) in enumerate(shapes)]
+    b = N.Batch(abcds, shapes)
+    ins = [torch.from_numpy(f).to(torch.complex64).cuda() for f in fields]
+    outs = [torch.empty_like(x) for x in ins]
+    b.bind(ins, outs)
+    return b, shapes, abcds, fields, ins, outs
+
+
+def test_batch_matches_single_plans_and_oracle(N, batch_case):
+    b, shapes, abcds, fields, ins, outs = batch_case
+    b.forward()
+    torch.cuda.synchronize()
+    for k, (nx, ny) in enumerate(shapes):
+        plan = N.Plan(abcds[k], nx, ny)
+        ref = plan.forward(ins[k])
+        torch.cuda.synchronize()
+        got = outs[k].cpu().numpy().astype(np.complex128)
+        single = ref.cpu().numpy().astype(np.complex128)
+        assert O.rel_l2(got, single) < 2e-6, (k, nx, ny)
+        # the batch's own plan for this field equals a standalone plan
+        np.testing.assert_allclose(b.params(k)["H"], plan.params()["H"], atol=0)
+        if nx * ny <= 256 * 256:
+            params = O.decompose(b.info(k)["abcd"], b.params(k)["H"])
+            ref_o = O.forward(fields[k], params, b.dx[k], b.dy[k])
+            assert O.rel_l2(got, ref_o) < 2e-5, (k, nx, ny)
+        plan.close()
+
+
+def test_batch_graph_and_each_agree(N, batch_case):
+    b, shapes, abcds, fields, ins, outs = batch_case
+    b.forward()
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    # run again: counters are reset every run
+    b.forward()
+    torch.cuda.synchronize()
+    for a, o in zip(first, outs):
+        assert torch.equal(a, o)
+    # graph capture replays the same launches
+    s = torch.cuda.Stream()
+    b.capture(s)
+    for o in outs:
+        o.zero_()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        b.forward(stream=s)
+    s.synchronize()
+    for a, o in zip(first, outs):
+        assert torch.equal(a, o)
+    # per-field launches through the single-field kernels
+    b.forward_each()
+    torch.cuda.synchronize()
+    for a, o in zip(first, outs):
+        assert O.rel_l2(o.cpu().numpy().astype(np.complex128), a.cpu().numpy().astype(np.complex128)) < 2e-6
+
+
+def test_batch_rejects_unsupported_sizes(N):
+    with pytest.raises(N.NslctError) as exc:
+        N.Batch([I.random_symplectic_abcd(1)], [(48, 64)])
+    assert exc.value.code == N.NSLCT_E_SIZE
