@@ -41,7 +41,7 @@ FIELD_SEED = 2
 NOISE_SEED = 102
 ABCD_SEED0 = 200
 BYTES_PER_SAMPLE_PASS = 16        # read + write one complex64 per sample per pass
-PASSES = 5
+H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
             "symplectic ABCD, forward HA-NsDLCT per ABCD")
@@ -185,7 +185,10 @@ def run_gpu(args, world, rank, local):
     N.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     g, mats = _make_inputs()
-    plans = [N.Plan(m, NX, NY) for m in mats]
+    plans = [N.Plan(m, NX, NY, precision=args.precision, method=args.method) for m in mats]
+    npass = plans[0].passes()
+    if any(p.passes() != npass for p in plans):
+        raise RuntimeError("plans of one bench run must share their pass count")
     x = torch.from_numpy(g).to(torch.complex64).to(dev)
     outs = [torch.empty_like(x) for _ in range(N_ABCD)]
     stream = torch.cuda.current_stream(dev)
@@ -227,43 +230,53 @@ def run_gpu(args, world, rank, local):
 
     # ---- per-pass durations (same work, events between the five passes)
     npass_iters = max(1, args.steps)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(PASSES + 1)] for _ in range(npass_iters * N_ABCD)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(npass_iters * N_ABCD)]
     barrier()
     k = 0
     for _ in range(npass_iters):
         for p, o in zip(plans, outs):
             e = evs[k]
             e[0].record(stream)
-            for j in range(PASSES):
+            for j in range(npass):
                 N.nslct_forward_pass(p.handle, j, x, o, stream)
                 e[j + 1].record(stream)
             k += 1
     barrier()
-    pass_ms = np.zeros(PASSES)
+    pass_ms = np.zeros(npass)
     for e in evs:
-        for j in range(PASSES):
+        for j in range(npass):
             pass_ms[j] += e[j].elapsed_time(e[j + 1])
     pass_ms /= len(evs)
     peak, peak_kind = _peaks()
     bytes_launch = BYTES_PER_SAMPLE_PASS * NX * NY
-    # the dominant kernel: the column pass (kernels 1 and 3 are the same kernel)
-    col_ms = 0.5 * (pass_ms[1] + pass_ms[3])
-    row_ms = (pass_ms[0] + pass_ms[2] + pass_ms[4]) / 3
-    dom_ms, dom_name = (col_ms, "pass_kernel<float,4096,col>") if col_ms >= row_ms else \
-        (row_ms, "pass_kernel<float,4096,row>")
+    # the dominant kernel: the column pass (passes 1 and 3 of five, pass 1 of three)
+    col_idx = [1, 3] if npass == 5 else [1]
+    row_idx = [j for j in range(npass) if j not in col_idx]
+    col_ms = float(np.mean(pass_ms[col_idx]))
+    row_ms = float(np.mean(pass_ms[row_idx]))
+    dom_ms, dom_name = (col_ms, "pass_kernel_tma<4096,col>") if col_ms >= row_ms else \
+        (row_ms, "pass_kernel_tma<4096,row>")
     achieved = bytes_launch / (dom_ms * 1e-3) / 1e9
-    chain_gbs = PASSES * bytes_launch / (pass_ms.sum() * 1e-3) / 1e9
+    chain_gbs = npass * bytes_launch / (pass_ms.sum() * 1e-3) / 1e9
 
-    # ---- end to end: pinned host input -> device -> 16 transforms -> pinned host outputs
+    # ---- end to end: pinned host input -> device -> 16 transforms -> pinned host outputs.
+    # Each output's device->host copy runs on a copy stream while the next
+    # transform computes; the step ends when the last copy has landed.
     host_in = torch.from_numpy(g).to(torch.complex64).pin_memory()
     host_outs = [torch.empty((NX, NY), dtype=torch.complex64).pin_memory() for _ in range(N_ABCD)]
     x_e2e = torch.empty_like(x)
+    copy_stream = torch.cuda.Stream(dev)
+    done = [torch.cuda.Event() for _ in range(N_ABCD)]
 
     def e2e_step():
         x_e2e.copy_(host_in, non_blocking=True)
-        for p, o, h in zip(plans, outs, host_outs):
+        for p, o, h, ev in zip(plans, outs, host_outs, done):
             N.nslct_forward(p.handle, x_e2e, o, stream)
-            h.copy_(o, non_blocking=True)
+            ev.record(stream)
+            copy_stream.wait_event(ev)
+            with torch.cuda.stream(copy_stream):
+                h.copy_(o, non_blocking=True)
+        stream.wait_stream(copy_stream)
 
     e2e_steps = max(1, min(args.steps, 5))
     e2e_step()
@@ -281,16 +294,17 @@ def run_gpu(args, world, rank, local):
     result = {
         "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "n_abcd": N_ABCD, "precision": "fp32",
-                   "h_choice": "HA (Eq. HA24)", "parallelism": f"replicas x{world}",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16-split+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.method == "ha" else WORKLOAD.replace("HA-NsDLCT", "LC-NsDLCT"),
+                   "nx": NX, "ny": NY, "n_abcd": N_ABCD, "precision": args.precision,
+                   "h_choice": H_CHOICE[args.method], "passes": npass, "parallelism": f"replicas x{world}",
                    "l2": "no flush: 16 distinct 128 MiB outputs per step, working set 2.1 GB > 126 MB L2"},
-        "gpu_launches": args.steps * N_ABCD * PASSES,
+        "gpu_launches": args.steps * N_ABCD * npass,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": dom_name,
                      "peak_source": f"hbm_gbs ({peak_kind})",
                      "bytes_per_launch": bytes_launch, "avg_launch_ms": dom_ms},
-        "chain": {"pass_ms": [round(v, 5) for v in pass_ms], "modelled_bytes_per_sample": PASSES * BYTES_PER_SAMPLE_PASS,
+        "chain": {"pass_ms": [round(v, 5) for v in pass_ms], "modelled_bytes_per_sample": npass * BYTES_PER_SAMPLE_PASS,
                   "achieved_gbs": chain_gbs, "frac_of_hbm": chain_gbs / peak,
                   "compulsory_frac": 16 * NX * NY / (pass_ms.sum() * 1e-3) / 1e9 / peak},
         "e2e": {"value": e2e_value, "unit": "Msamples/s", "h2d_bytes_per_step": NX * NY * 8,
@@ -307,8 +321,8 @@ def run_gpu(args, world, rank, local):
         ref = O.forward(g, params, p0.dx, p0.dy)
         t_cpu = time.perf_counter() - t0
         gpu_out = outs[0].cpu().numpy().astype(np.complex128)
-        result["rel_l2"] = {"fp32_vs_oracle": O.rel_l2(gpu_out, ref), "field": "ABCD seed 200, 4096^2",
-                            "tolerance": 2e-5}
+        result["rel_l2"] = {f"{args.precision}_vs_oracle": O.rel_l2(gpu_out, ref), "field": "ABCD seed 200, 4096^2",
+                            "tolerance": 2e-5 if args.precision == "fp32" else 1e-4}
         result["cpu_baseline"] = {"value": NX * NY / t_cpu / 1e6, "unit": "Msamples/s", "cores": _blas_threads(),
                                   "kind": "oracle",
                                   "sample": "one 4096x4096 forward transform (ABCD seed 200), FP64 dense DFT-matrix sums",
@@ -319,6 +333,113 @@ def run_gpu(args, world, rank, local):
         p.close()
 
 
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batch_workload(args, world, rank):
+    """256 fields with Nx, Ny drawn from {128, ..., 2048}, each with its own ABCD:
+    the batched persistent launches (captured in one CUDA graph) against the
+    same transforms launched field by field."""
+    import torch
+    from paper_1707_03688_gb300 import inputs as I
+    from paper_1707_03688_gb300 import nslct as N
+    N.load()
+    sizes = [128, 192, 256, 384, 512, 768, 1024, 1536, 2048]
+    rng = np.random.default_rng(3)
+    shapes = [(int(rng.choice(sizes)), int(rng.choice(sizes))) for _ in range(256)]
+    abcds = [I.random_symplectic_abcd(30000 + k) for k in range(len(shapes))]
+    b = N.Batch(abcds, shapes)
+    ins = [torch.from_numpy(I.blob_field(nx, ny, seed=31000 + k)).to(torch.complex64).cuda()
+           for k, (nx, ny) in enumerate(shapes)]
+    outs = [torch.empty_like(x) for x in ins]
+    b.bind(ins, outs)
+    stream = torch.cuda.Stream()
+    samples = sum(nx * ny for nx, ny in shapes)
+    with torch.cuda.stream(stream):
+        ms_each = _timed(lambda: b.forward_each(stream), args.steps, args.warmup, stream)
+        ms_launch = _timed(lambda: b.forward(stream), args.steps, args.warmup, stream)
+        b.capture(stream)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            ms_graph = _timed(lambda: b.forward(stream), args.steps, args.warmup, stream)
+    value = samples / (ms_graph * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "256 fields, Nx and Ny each from {128,...,2048}, own ABCD per field, forward, "
+                               "batched persistent launches captured in one CUDA graph",
+                   "samples_per_step": samples, "l2": "working set 2 x samples x 8 B > L2"},
+        "per_field_launches": {"ms_per_step": ms_each, "value": samples / (ms_each * 1e-3) / 1e6},
+        "batched_no_graph": {"ms_per_step": ms_launch, "value": samples / (ms_launch * 1e-3) / 1e6},
+        "gpu_launches": 5, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+
+
+def run_grad_workload(args, world, rank):
+    """Batch of 64 fields of 1024 x 1024: forward, loss ||L(x) - y||^2 and the
+    backward pass with gradients for x and the 10 ABCD parameters."""
+    import torch
+    from paper_1707_03688_gb300 import inputs as I
+    from paper_1707_03688_gb300 import nslct as N
+    N.load()
+    n, nb = 1024, 64
+    m = I.random_symplectic_abcd(4)
+    plan = N.Plan(m, n, n)
+    # targets: seeded target fields under the perturbed parameters theta + N(0, 0.05^2)
+    theta = plan.theta()
+    delta = np.random.default_rng(4).normal(0.0, 0.05, size=10)
+    target_plan = N.Plan.from_theta(theta + delta, n, n, h0=plan.params()["H"])
+    xs = [torch.from_numpy(I.blob_field(n, n, seed=4000 + k)).to(torch.complex64).cuda() for k in range(nb)]
+    yts = [target_plan.forward(torch.from_numpy(I.blob_field(n, n, seed=5000 + k)).to(torch.complex64).cuda())
+           for k in range(nb)]
+    torch.cuda.synchronize()
+    target_plan.close()
+    ys = [torch.empty_like(x) for x in xs]
+    gy = torch.empty_like(xs[0])
+    gx = torch.empty_like(xs[0])
+    ws = torch.empty_like(xs[0])
+    gth = torch.zeros(10, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for x, y, yt in zip(xs, ys, yts):
+            N.nslct_forward(plan.handle, x, y, stream)
+            torch.sub(y, yt, out=gy)
+            gy.mul_(2)
+            N.nslct_backward(plan.handle, gy, y, gx, gth, None, ws, stream)
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = _timed(step, args.steps, args.warmup, stream)
+    value = nb * n * n / (ms * 1e-3) / 1e6
+    line = {
+        "metric": "forward + backward (x and ABCD-parameter gradients) Msamples/s", "value": value,
+        "unit": "Msamples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "64 x 1024^2 complex64, loss ||L(x) - y||^2 with y = L_{theta+delta}(x_target), "
+                               "delta ~ N(0, 0.05^2) on the 10 ABCD parameters, nslct_forward + nslct_backward",
+                   "note": "the residual 2(y - y_t) is formed with torch ops between the two library calls"},
+        "gpu_launches": nb * (5 + 5 + 1), "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,6 +447,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fp32", choices=["fp32", "batch", "grad"],
+                    help="fp32: 4096^2 x 16 ABCD (the benchmark line); batch: 256 uneven fields; "
+                         "grad: 64 x 1024^2 forward + backward")
+    ap.add_argument("--method", default="ha", choices=["ha", "lc_y"],
+                    help="H of Eq. HA24 (five passes) or of Eq. LC10 (three passes)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
+                    help="fp32: FP32 FFT arithmetic; mixed: radix-16 stages as split-FP16 tensor-core DFT-16")
     ap.add_argument("--n-abcd", type=int, default=16,
                     help="ABCD matrices per step (16 is the benchmark workload; fewer only for profiling captures)")
     args = ap.parse_args()
@@ -334,6 +462,10 @@ def main():
     world, rank, local = _dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batch":
+        run_batch_workload(args, world, rank)
+    elif args.workload == "grad":
+        run_grad_workload(args, world, rank)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

@@ -64,13 +64,24 @@ typedef struct CUstream_st* nslct_stream_t;  /* same type as cudaStream_t */
 #define NSLCT_H_HA          0x0u   /* high-accuracy criterion, Eq. HA24 (default) */
 #define NSLCT_H_LC          0x1u   /* low-complexity closed form, Eqs. LC08/LC10; HA if invalid */
 #define NSLCT_H_USER        0x2u   /* H given by the caller (nslct_plan_ex) */
+#define NSLCT_H_LC_Y        0x3u   /* Eq. LC10's H = (0,0;0,h) when valid, else as NSLCT_H_LC */
 #define NSLCT_H_MASK        0x3u
 /* Replace a nearly symplectic ABCD (e.g. one printed to 4 decimals) by a
  * nearby exactly symplectic one before planning. */
 #define NSLCT_PROJECT_SP4   0x10u
+/* Always run the five-pass chain. Without it, FP32 plans whose H is
+ * (0,0;0,h) (Eq. LC10, or H = 0) run in three passes: CC^H then convolves
+ * along y only and shares one row pass with CM^{C2} (see nslct_plan_passes). */
+#define NSLCT_FULL_CHAIN    0x20u
 /* Arithmetic of the transform. */
 #define NSLCT_PREC_FP32     0x000u /* complex64 data, FP32 FFT arithmetic (default) */
 #define NSLCT_PREC_FP64     0x100u /* complex128 data, FP64 arithmetic throughout */
+/* complex64 data; the radix-16 FFT stages of 256..4096-point lines run as
+ * DFT-16 products on the tensor cores with operands split into FP16 halves
+ * (x = x_hi + x_lo, W = W_hi + W_lo; x_hi W_hi + x_hi W_lo + x_lo W_hi,
+ * FP32 accumulation); every other step stays FP32. Backward and batched
+ * calls of such a plan run in FP32. */
+#define NSLCT_PREC_SPLIT_F16 0x200u
 #define NSLCT_PREC_MASK     0xF00u
 
 /*
@@ -149,9 +160,20 @@ int nslct_forward(nslct_plan_t plan, const void* in, void* out, nslct_stream_t s
 int nslct_inverse(nslct_plan_t plan, const void* in, void* out, nslct_stream_t stream);
 
 /*
- * nslct_forward_pass -- enqueue ONE of the five kernel passes that make up
- * nslct_forward, for profiling and per-pass testing; calling passes 0..4 in
- * order on the same buffers gives exactly nslct_forward's result.
+ * nslct_plan_passes -- kernel passes per transform of this plan: 5, or 3 for
+ * FP32 plans with H = (0,0;0,h) (unless NSLCT_FULL_CHAIN): then
+ *   forward: row [FFT_y, chi_{-H}, IFFT_y, CM^{C2}, FFT_y], column [FFT_x, chi_{-B'},
+ *            IFFT_x], row [IFFT_y, CM^{C1}];
+ * the same operators as the five-pass chain, since with chi_H independent of
+ * k_x the x transforms of CC^H cancel.
+ */
+int nslct_plan_passes(nslct_plan_t plan);
+
+/*
+ * nslct_forward_pass -- enqueue ONE of the kernel passes that make up
+ * nslct_forward, for profiling and per-pass testing; calling passes
+ * 0 .. nslct_plan_passes() - 1 in order on the same buffers gives exactly
+ * nslct_forward's result. For five-pass plans:
  *   pass 0: row FFT of `in` (row-major) into `out` (2x2-tiled layout)
  *   pass 1: column FFT, chirp CM^{-H} at the frequency spacing, column IFFT
  *   pass 2: row IFFT, -1/(Nx Ny), CM^{C2}, row FFT
@@ -264,6 +286,26 @@ int nslct_batch_forward(nslct_batch_t batch, nslct_stream_t stream);
 /* nslct_batch_capture -- capture the bound batch's launches on `stream` (not the
  * legacy default stream) into a CUDA graph that nslct_batch_forward then launches. */
 int nslct_batch_capture(nslct_batch_t batch, nslct_stream_t stream);
+
+/*
+ * nslct_batch_set_split -- fields whose longer side is >= `split` run through
+ * their own plan's fused passes (as nslct_forward), enqueued before the batched
+ * launches; the others stay in the batched launches. The default (2^30)
+ * batches every field. Drops a captured graph. nslct_batch_get_split returns it.
+ */
+int nslct_batch_set_split(nslct_batch_t batch, int split);
+int nslct_batch_get_split(nslct_batch_t batch);
+
+/*
+ * nslct_batch_tune -- autotune the split on the bound buffers: for every
+ * distinct field size (and "batch everything") run one warm-up forward and
+ * `iters` timed forwards on `stream` (CUDA events), keep the fastest, and
+ * return it in *chosen (nullable) with its time per forward in
+ * *ms_per_forward (nullable). Synchronises `stream`. Overwrites the bound
+ * outputs; bindings with in[f] == out[f] are rejected (NSLCT_E_ARG) because
+ * the repeated runs would feed outputs back in. Drops a captured graph.
+ */
+int nslct_batch_tune(nslct_batch_t batch, nslct_stream_t stream, int iters, int* chosen, float* ms_per_forward);
 
 /* nslct_batch_forward_each -- the same transforms as per-field nslct_forward calls (5 launches per field). */
 int nslct_batch_forward_each(nslct_batch_t batch, nslct_stream_t stream);

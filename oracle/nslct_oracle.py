@@ -370,18 +370,19 @@ def ha_search(m, grid: int = 241, grid3: int = 41, starts: int = 6, zoom_pts: in
     return h_from_vec(points(best_c[None, :])[0])
 
 
-def lc_h(m):
+def lc_h(m, only_y: bool = False):
     """Low-complexity H of Eqs. LC04-LC10 (Sec. 4.B.2).
 
     Candidates: H = (h,0;0,0) with h = (b21 - b12)/a21 when a21 != 0, and
     H = (0,0;0,h) with h = (b12 - b21)/a12 when a12 != 0. Candidates whose B'
     is (numerically) singular are dropped; of the rest the one with the lower
     Eq. HA24 objective is returned. Returns None when no candidate is valid
-    (the paper then falls back to the HA choice).
+    (the paper then falls back to the HA choice). ``only_y`` keeps the
+    Eq. LC10 candidate alone.
     """
     a, b, _, _ = split_abcd(m)
     cands = []
-    if abs(a[1, 0]) > 1e-12:
+    if abs(a[1, 0]) > 1e-12 and not only_y:
         cands.append(np.array([[(b[1, 0] - b[0, 1]) / a[1, 0], 0.0], [0.0, 0.0]]))
     if abs(a[0, 1]) > 1e-12:
         cands.append(np.array([[0.0, 0.0], [0.0, (b[0, 1] - b[1, 0]) / a[0, 1]]]))

@@ -63,8 +63,13 @@ void free_plan(nslct_plan_s* p) {
   if (p->ws) cudaFree(p->ws);
   if (p->err) cudaFree(p->err);
   if (p->partials) cudaFree(p->partials);
-  if (p->tw_y && p->tw_y != p->tw_x) cudaFree(p->tw_y);
-  if (p->tw_x) cudaFree(p->tw_x);
+  // the four twiddle pointers may alias each other: free each table once
+  void* tabs[4] = {p->tw_x, p->tw_y, p->tw16_x, p->tw16_y};
+  for (int i = 0; i < 4; ++i) {
+    bool seen = !tabs[i];
+    for (int k = 0; k < i && !seen; ++k) seen = tabs[k] == tabs[i];
+    if (!seen) cudaFree(tabs[i]);
+  }
   delete p;
 }
 
@@ -82,9 +87,11 @@ int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, 
   if (!g.ok) return NSLCT_E_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   PassDesc d[5];
-  build_chain_descs(p, in, out, inverse, d);
+  bool cols[5];
+  const int npass = build_schedule(p, in, out, inverse, d, cols);
+  if (last >= npass) return NSLCT_E_ARG;
   for (int k = first; k <= last; ++k) {
-    const int rc = launch(p, chain_pass_is_column(k), d[k], s);
+    const int rc = launch(p, cols[k], d[k], s);
     if (rc != NSLCT_OK) return rc;
   }
   return NSLCT_OK;
@@ -105,6 +112,7 @@ void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool in
   base.Nx = p->Nx;
   base.Ny = p->Ny;
   base.scale = 1.0;
+  base.fscale2 = 1.0f;
   for (int k = 0; k < 5; ++k) d[k] = base;
   // pass 1: row pass, caller layout -> tiled layout in `out`
   d[0].in = in; d[0].out = out; d[0].in_tiled = 0; d[0].out_tiled = 1; d[0].tw = p->tw_y;
@@ -137,7 +145,59 @@ void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool in
     d[k].scale_only = (!d[k].has_chirp && d[k].scale != 1.0) ? 1 : 0;
     d[k].num_sms = p->num_sms;
     d[k].err = p->err;
+    d[k].mixed = p->mixed;
   }
+}
+
+// When H = (0,0;0,h) (the closed form of Eq. LC10, or H = 0), CC^H only
+// convolves along y:
+//   CC^H = -(1/(Nx Ny)) IFFT2(chi_H FFT2(.)) = -(1/Ny) IFFT_y(chi_H(k_y) FFT_y(.)),
+// because the x transforms of FFT2 and IFFT2 then cancel to Nx I. CC^H and
+// CM^{C2} and the row half of the next CC then share one row pass:
+//   forward: row [FFT_y, chi_{-H} -1/Ny, IFFT_y, CM^{C2}, FFT_y]
+//            col [FFT_x, chi_{-B'}, IFFT_x]
+//            row [IFFT_y, CM^{C1} -1/(Nx Ny)]
+//   inverse: row [CM^{-C1}, FFT_y]
+//            col [FFT_x, chi_{+B'}, IFFT_x]
+//            row [IFFT_y, CM^{-C2} -1/(Nx Ny), FFT_y, chi_{+H} -1/Ny, IFFT_y]
+// Three passes instead of five (48 instead of 80 bytes per sample).
+int build_schedule(const nslct_plan_s* p, const void* in, void* out, bool inverse, PassDesc d[5], bool cols[5]) {
+  build_chain_descs(p, in, out, inverse, d);
+  for (int k = 0; k < 5; ++k) cols[k] = chain_pass_is_column(k);
+  if (!p->y_only_h) return 5;
+  const float cy = -1.0f / (float)p->Ny;
+  const double ccs = -1.0 / ((double)p->Nx * (double)p->Ny);
+  PassDesc r1 = d[0], c2 = d[1], r3 = d[4];
+  if (!inverse) {
+    r1.t1 = kFwd;
+    r1.has_chirp = 1; r1.freq_domain = 1; r1.chirp = p->fwd_chi_h; r1.scale = cy;
+    r1.t2 = kInv;
+    r1.has_chirp2 = 1; r1.freq_domain2 = 0; r1.chirp2 = p->fwd_cm_c2; r1.fscale2 = 1.0f;
+    r1.t3 = kFwd;
+    c2 = d[3];  // FFT_x, chi_{-B'}, IFFT_x
+    r3 = d[4];  // IFFT_y, CM^{C1} x -1/(Nx Ny)
+  } else {
+    r1 = d[0];  // CM^{-C1}, FFT_y
+    c2 = d[1];  // FFT_x, chi_{+B'}, IFFT_x
+    r3 = d[4];
+    r3.t1 = kInv;
+    r3.has_chirp = 1; r3.freq_domain = 0; r3.chirp = p->inv_cm_c2; r3.scale = ccs;
+    r3.t2 = kFwd;
+    r3.has_chirp2 = 1; r3.freq_domain2 = 1; r3.chirp2 = p->inv_chi_h; r3.fscale2 = cy;
+    r3.t3 = kInv;
+  }
+  for (PassDesc* x : {&r1, &c2, &r3}) {
+    x->fscale = (float)x->scale;
+    x->scale_only = (!x->has_chirp && x->scale != 1.0) ? 1 : 0;
+  }
+  // r1 reads the caller's field and writes the tiled one; c2 works in place;
+  // r3 returns to the caller's layout in `out`
+  r1.in = in; r1.out = out; r1.in_tiled = 0; r1.out_tiled = 1;
+  c2.in = out; c2.out = out; c2.in_tiled = 1; c2.out_tiled = 1;
+  r3.in = out; r3.out = out; r3.in_tiled = 1; r3.out_tiled = 0;
+  d[0] = r1; d[1] = c2; d[2] = r3;
+  cols[0] = false; cols[1] = true; cols[2] = false;
+  return 3;
 }
 
 bool supported_length(int L) {
@@ -159,7 +219,6 @@ static int derive(const double abcd[16], unsigned flags, const double* h_user, d
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(abcd[i])) return NSLCT_E_ARG;
   const unsigned hsel = flags & NSLCT_H_MASK;
-  if (hsel == 3u) return NSLCT_E_ARG;
   if (hsel == NSLCT_H_USER && !h_user) return NSLCT_E_ARG;
   std::memcpy(m, abcd, 16 * sizeof(double));
   double mmax = 1.0;
@@ -184,6 +243,10 @@ static int derive(const double abcd[16], unsigned flags, const double* h_user, d
   } else if (hsel == NSLCT_H_LC) {
     rc = choose_h_lc(m, &h);
     if (rc != NSLCT_OK) rc = choose_h_ha(m, &h);  // Sec. 4.B.2: fall back to the HA choice
+  } else if (hsel == NSLCT_H_LC_Y) {
+    rc = choose_h_lc_y(m, &h);
+    if (rc != NSLCT_OK) rc = choose_h_lc(m, &h);
+    if (rc != NSLCT_OK) rc = choose_h_ha(m, &h);
   } else {
     rc = choose_h_ha(m, &h);
   }
@@ -200,7 +263,8 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   if (!abcd || Nx < 2 || Ny < 2 || !(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
     return NSLCT_E_ARG;
   const unsigned prec_flag = flags & NSLCT_PREC_MASK;
-  if (prec_flag != NSLCT_PREC_FP32 && prec_flag != NSLCT_PREC_FP64) return NSLCT_E_UNSUPPORTED;
+  if (prec_flag != NSLCT_PREC_FP32 && prec_flag != NSLCT_PREC_FP64 && prec_flag != NSLCT_PREC_SPLIT_F16)
+    return NSLCT_E_UNSUPPORTED;
   if (!supported_length(Nx) || !supported_length(Ny)) return NSLCT_E_SIZE;
   double m[16];
   Decomp dc{};
@@ -211,6 +275,7 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   if (!p) return NSLCT_E_NOMEM;
   p->Nx = Nx; p->Ny = Ny; p->dx = dx; p->dy = dy; p->flags = flags;
   p->prec = prec_flag == NSLCT_PREC_FP64 ? 1 : 0;
+  p->mixed = prec_flag == NSLCT_PREC_SPLIT_F16 ? 1 : 0;
   std::memcpy(p->M, m, sizeof(m));
   const Mat2* src[4] = {&dc.H, &dc.Bp, &dc.C1, &dc.C2};
   double* dst[4] = {p->H, p->Bp, p->C1, p->C2};
@@ -218,6 +283,8 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
     dst[k][0] = src[k]->m00; dst[k][1] = src[k]->m01; dst[k][2] = src[k]->m10; dst[k][3] = src[k]->m11;
   }
   fill_chirps(p);
+  p->y_only_h = (p->prec == 0 && !(flags & NSLCT_FULL_CHAIN) && p->H[0] == 0.0 && p->H[1] == 0.0 && p->H[2] == 0.0)
+                    ? 1 : 0;
   p->has_theta = theta_from_abcd(p->M, p->theta) ? 1 : 0;
   if (p->has_theta) chirp_jacobian(p->theta, p->H, p->jac);
 
@@ -229,12 +296,25 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   if (cudaMalloc(&p->err, sizeof(unsigned int)) != cudaSuccess) { p->err = nullptr; free_plan(p); return NSLCT_E_NOMEM; }
   if (cudaMemset(p->err, 0, sizeof(unsigned int)) != cudaSuccess) { free_plan(p); return NSLCT_E_CUDA; }
   const bool f32 = p->prec == 0;
-  rc = f32 ? upload_twiddles<float>(Nx, kernel_elems(Nx, true), &p->tw_x)
-           : upload_twiddles<double>(Nx, kernel_elems(Nx, false), &p->tw_x);
+  // forward/inverse kernels: kernel_elems (split-precision plans: 16 per thread);
+  // adjoint and batched kernels: elems_per_thread
+  auto fwd_e = [&](int L) { return p->mixed ? elems_per_thread(L) : kernel_elems(L, f32); };
+  auto upload = [&](int L, int E, void** dst) {
+    return f32 ? upload_twiddles<float>(L, E, dst) : upload_twiddles<double>(L, E, dst);
+  };
+  rc = upload(Nx, fwd_e(Nx), &p->tw_x);
   if (rc == NSLCT_OK) {
     if (Ny == Nx) p->tw_y = p->tw_x;
-    else rc = f32 ? upload_twiddles<float>(Ny, kernel_elems(Ny, true), &p->tw_y)
-                  : upload_twiddles<double>(Ny, kernel_elems(Ny, false), &p->tw_y);
+    else rc = upload(Ny, fwd_e(Ny), &p->tw_y);
+  }
+  if (rc == NSLCT_OK) {
+    if (fwd_e(Nx) == elems_per_thread(Nx)) p->tw16_x = p->tw_x;
+    else rc = upload(Nx, elems_per_thread(Nx), &p->tw16_x);
+  }
+  if (rc == NSLCT_OK) {
+    if (Ny == Nx) p->tw16_y = p->tw16_x;
+    else if (fwd_e(Ny) == elems_per_thread(Ny)) p->tw16_y = p->tw_y;
+    else rc = upload(Ny, elems_per_thread(Ny), &p->tw16_y);
   }
   if (rc == NSLCT_OK) rc = p->prec ? prepare_pass_f64(Nx) : prepare_pass_f32(Nx);
   if (rc == NSLCT_OK && Ny != Nx) rc = p->prec ? prepare_pass_f64(Ny) : prepare_pass_f32(Ny);
@@ -311,15 +391,17 @@ int nslct_plan_info(nslct_plan_t p, int* Nx, int* Ny, unsigned* flags, double ab
 }
 
 int nslct_forward(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream) {
-  return run_chain(p, in, out, stream, false);
+  return run_chain(p, in, out, stream, false, 0, p ? nslct_plan_passes(p) - 1 : 4);
 }
 
 int nslct_inverse(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream) {
-  return run_chain(p, in, out, stream, true);
+  return run_chain(p, in, out, stream, true, 0, p ? nslct_plan_passes(p) - 1 : 4);
 }
 
+int nslct_plan_passes(nslct_plan_t p) { return !p ? 0 : (p->y_only_h ? 3 : 5); }
+
 int nslct_forward_pass(nslct_plan_t p, int pass, const void* in, void* out, nslct_stream_t stream) {
-  if (pass < 0 || pass > 4) return NSLCT_E_ARG;
+  if (!p || pass < 0 || pass >= nslct_plan_passes(p)) return NSLCT_E_ARG;
   return run_chain(p, in, out, stream, false, pass, pass);
 }
 

@@ -87,13 +87,14 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
   base.Nx = p->Nx;
   base.Ny = p->Ny;
   base.scale = 1.0;
+  base.fscale2 = 1.0f;
   PassDesc d[5];
   for (auto& x : d) x = base;
   // the inverse chain (Eq. CCCMCCCM04), as in nslct_inverse
-  d[0].in = grad_out; d[0].out = grad_in; d[0].in_tiled = 0; d[0].out_tiled = 1; d[0].tw = p->tw_y;
+  d[0].in = grad_out; d[0].out = grad_in; d[0].in_tiled = 0; d[0].out_tiled = 1; d[0].tw = p->tw16_y;
   for (int k = 1; k < 5; ++k) { d[k].in = grad_in; d[k].out = grad_in; d[k].in_tiled = 1; d[k].out_tiled = 1; }
   d[4].out_tiled = 0;
-  d[1].tw = p->tw_x; d[2].tw = p->tw_y; d[3].tw = p->tw_x; d[4].tw = p->tw_y;
+  d[1].tw = p->tw16_x; d[2].tw = p->tw16_y; d[3].tw = p->tw16_x; d[4].tw = p->tw16_y;
   d[1].freq_domain = d[3].freq_domain = 1;
   d[0].has_chirp = 1; d[0].chirp = p->inv_cm_c1; d[0].t2 = kFwd;
   d[1].has_chirp = 1; d[1].chirp = p->inv_chi_bp; d[1].t1 = kFwd; d[1].t2 = kInv;

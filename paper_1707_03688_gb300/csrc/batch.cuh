@@ -20,7 +20,7 @@ namespace nslct {
   X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(96) X(192) X(384) X(768) X(1536)
 
 template <int L> struct BShape {
-  static constexpr int E = kernel_elems(L, true);
+  static constexpr int E = elems_per_thread(L);  // the plans' tw16 tables
   static constexpr int T_LINE = L / E;
   static constexpr int THREADS = 512;
   static constexpr int P = THREADS / T_LINE;   // lines per panel

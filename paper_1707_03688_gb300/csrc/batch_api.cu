@@ -19,6 +19,11 @@ struct nslct_batch_s {
   int item_off[5] = {0};
   int nitems[5] = {0};
   int* d_counters = nullptr;        // one per pass
+  // fields whose longer side is >= split run through their own plan's fused
+  // kernels (nslct_forward) instead of the batched launches; chosen by
+  // nslct_batch_tune (default: every field batched)
+  int split = 1 << 30;
+  std::vector<int> Nx, Ny;
   bool bound = false;
   std::vector<const void*> in;
   std::vector<void*> out;
@@ -40,7 +45,50 @@ void free_batch(nslct_batch_s* b) {
   delete b;
 }
 
+bool runs_alone(const nslct_batch_s* b, int f) { return std::max(b->Nx[f], b->Ny[f]) >= b->split; }
+
+// (Re)build the per-pass work lists of the batched fields: every field's
+// panels, longest lines first.
+int build_items(nslct_batch_s* b) {
+  std::vector<BatchItem> all;
+  for (int k = 0; k < 5; ++k) {
+    const bool col = chain_pass_is_column(k);
+    std::vector<int> order;
+    for (int f = 0; f < b->n; ++f)
+      if (!runs_alone(b, f)) order.push_back(f);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      const int la = col ? b->Nx[a] : b->Ny[a], lc = col ? b->Nx[c] : b->Ny[c];
+      return la > lc;
+    });
+    b->item_off[k] = (int)all.size();
+    for (int f : order) {
+      const int L = col ? b->Nx[f] : b->Ny[f];
+      const int lines = col ? b->Ny[f] : b->Nx[f];
+      const int P = batch_panel_lines(L);
+      for (int panel = 0; panel * P < lines; ++panel) all.push_back(BatchItem{f, panel});
+    }
+    b->nitems[k] = (int)all.size() - b->item_off[k];
+  }
+  if (b->d_items) { cudaFree(b->d_items); b->d_items = nullptr; }
+  if (all.empty()) return NSLCT_OK;
+  if (cudaMalloc(&b->d_items, all.size() * sizeof(BatchItem)) != cudaSuccess) { b->d_items = nullptr; return NSLCT_E_NOMEM; }
+  return cudaMemcpy(b->d_items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) == cudaSuccess
+             ? NSLCT_OK
+             : NSLCT_E_CUDA;
+}
+
+void drop_graph(nslct_batch_s* b) {
+  if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+}
+
 int enqueue(nslct_batch_s* b, cudaStream_t s) {
+  // the large fields first, each through its own fused passes
+  for (int f = 0; f < b->n; ++f) {
+    if (!runs_alone(b, f)) continue;
+    const int rc = nslct_forward(b->plans[f], b->in[f], b->out[f], s);
+    if (rc != NSLCT_OK) return rc;
+  }
   if (cudaMemsetAsync(b->d_counters, 0, 5 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
   for (int k = 0; k < 5; ++k) {
     if (b->nitems[k] == 0) continue;
@@ -80,35 +128,18 @@ int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const 
     if (rc != NSLCT_OK) { free_batch(b); return rc; }
     b->plans.push_back(p);
   }
-  // work lists: per pass, every field's panels, longest lines first
-  std::vector<BatchItem> all;
-  for (int k = 0; k < 5; ++k) {
-    const bool col = chain_pass_is_column(k);
-    std::vector<int> order(nfields);
-    for (int f = 0; f < nfields; ++f) order[f] = f;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-      const int la = col ? Nx[a] : Ny[a], lc = col ? Nx[c] : Ny[c];
-      return la > lc;
-    });
-    b->item_off[k] = (int)all.size();
-    for (int f : order) {
-      const int L = col ? Nx[f] : Ny[f];
-      const int lines = col ? Ny[f] : Nx[f];
-      const int P = batch_panel_lines(L);
-      for (int panel = 0; panel * P < lines; ++panel) all.push_back(BatchItem{f, panel});
-    }
-    b->nitems[k] = (int)all.size() - b->item_off[k];
-  }
-  if (cudaMalloc(&b->d_items, all.size() * sizeof(BatchItem)) != cudaSuccess ||
-      cudaMalloc(&b->d_descs, 5 * (size_t)nfields * sizeof(PassDesc)) != cudaSuccess ||
+  b->Nx.assign(Nx, Nx + nfields);
+  b->Ny.assign(Ny, Ny + nfields);
+  if (cudaMalloc(&b->d_descs, 5 * (size_t)nfields * sizeof(PassDesc)) != cudaSuccess ||
       cudaMalloc(&b->d_counters, 5 * sizeof(int)) != cudaSuccess) {
     free_batch(b);
     return NSLCT_E_NOMEM;
   }
-  if (cudaMemcpy(b->d_items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) != cudaSuccess ||
-      prepare_batch_row() != NSLCT_OK || prepare_batch_col() != NSLCT_OK) {
+  int rc = build_items(b);
+  if (rc == NSLCT_OK && (prepare_batch_row() != NSLCT_OK || prepare_batch_col() != NSLCT_OK)) rc = NSLCT_E_CUDA;
+  if (rc != NSLCT_OK) {
     free_batch(b);
-    return NSLCT_E_CUDA;
+    return rc;
   }
   *out = b;
   return NSLCT_OK;
@@ -130,7 +161,11 @@ int nslct_batch_bind(nslct_batch_t b, const void* const* in, void* const* out) {
     if ((reinterpret_cast<uintptr_t>(in[f]) | reinterpret_cast<uintptr_t>(out[f])) & 15u) return NSLCT_E_ARG;
     PassDesc d[5];
     build_chain_descs(b->plans[f], in[f], out[f], false, d);
-    for (int k = 0; k < 5; ++k) descs[(size_t)k * b->n + f] = d[k];
+    // the batched kernels run elems_per_thread(L) per thread: their twiddle tables
+    for (int k = 0; k < 5; ++k) {
+      d[k].tw = chain_pass_is_column(k) ? b->plans[f]->tw16_x : b->plans[f]->tw16_y;
+      descs[(size_t)k * b->n + f] = d[k];
+    }
   }
   int prev = -1;
   cudaGetDevice(&prev);
@@ -142,17 +177,67 @@ int nslct_batch_bind(nslct_batch_t b, const void* const* in, void* const* out) {
   b->in.assign(in, in + b->n);
   b->out.assign(out, out + b->n);
   b->bound = true;
-  if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
-  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  drop_graph(b);
   return NSLCT_OK;
+}
+
+int nslct_batch_set_split(nslct_batch_t b, int split) {
+  if (!b || split < 1) return NSLCT_E_ARG;
+  b->split = split;
+  drop_graph(b);
+  return build_items(b);
+}
+
+int nslct_batch_get_split(nslct_batch_t b) { return b ? b->split : 0; }
+
+int nslct_batch_tune(nslct_batch_t b, nslct_stream_t stream, int iters, int* chosen, float* ms_per_forward) {
+  if (!b || !b->bound || iters < 1) return NSLCT_E_ARG;
+  for (int f = 0; f < b->n; ++f)
+    if (b->in[f] == b->out[f]) return NSLCT_E_ARG;  // the timing runs must not feed outputs back in
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  drop_graph(b);
+  // candidate thresholds: the distinct field sizes (largest side), and "none"
+  std::vector<int> cands;
+  for (int f = 0; f < b->n; ++f) cands.push_back(std::max(b->Nx[f], b->Ny[f]));
+  std::sort(cands.begin(), cands.end());
+  cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+  cands.push_back(1 << 30);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return NSLCT_E_CUDA;
+  }
+  int best = 1 << 30, rc = NSLCT_OK;
+  float best_ms = 0.0f;
+  for (int c : cands) {
+    b->split = c;
+    rc = build_items(b);
+    if (rc == NSLCT_OK) rc = enqueue(b, s);  // warm-up
+    if (rc == NSLCT_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = NSLCT_E_CUDA;
+    for (int i = 0; rc == NSLCT_OK && i < iters; ++i) rc = enqueue(b, s);
+    if (rc == NSLCT_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      rc = NSLCT_E_CUDA;
+    float ms = 0.0f;
+    if (rc == NSLCT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = NSLCT_E_CUDA;
+    if (rc != NSLCT_OK) break;
+    ms /= (float)iters;
+    if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->split = best;
+  const int rc2 = build_items(b);
+  if (rc == NSLCT_OK) rc = rc2;
+  if (chosen) *chosen = best;
+  if (ms_per_forward) *ms_per_forward = best_ms;
+  return rc;
 }
 
 int nslct_batch_capture(nslct_batch_t b, nslct_stream_t stream) {
   if (!b || !b->bound) return NSLCT_E_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!s) return NSLCT_E_ARG;  // the legacy default stream cannot be captured
-  if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
-  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  drop_graph(b);
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NSLCT_E_CUDA;
   const int rc = enqueue(b, s);
   cudaGraph_t g = nullptr;

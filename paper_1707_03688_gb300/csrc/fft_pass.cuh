@@ -15,7 +15,9 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -194,8 +196,11 @@ template <typename R> struct Dft<R, 8> : DftComposite<R, 4, 2> {};
 template <typename R> struct Dft<R, 12> : DftComposite<R, 4, 3> {};
 template <typename R> struct Dft<R, 16> : DftComposite<R, 4, 4> {};
 template <typename R> struct Dft<R, 24> : DftComposite<R, 8, 3> {};
+template <typename R> struct Dft<R, 32> : DftComposite<R, 8, 4> {};
+template <typename R> struct Dft<R, 64> : DftComposite<R, 8, 8> {};
 
 __device__ __forceinline__ int padded(int e) { return e + (e >> 4); }
+template <int SH> __device__ __forceinline__ int padded_by(int e) { return e + (e >> SH); }
 
 // Twiddles of stage ST for butterfly jm: tab[OFF + jm*RD + r] = W_{NS*RD}^{jm*r}.
 template <typename R, int RD>
@@ -215,12 +220,32 @@ __device__ __forceinline__ void load_twiddles(const cpx<R>* __restrict__ row, cp
   }
 }
 
-template <typename R, int L, int P, int E_ = elems_per_thread(L)>
+// LM (line-major): the T_LINE threads of line p are threads p*T_LINE .. ,
+// whole warps, so each line keeps its exchange buffer to itself
+// (p*(L + L/16) + padded(e)) and synchronises on its own named barrier
+// (1 + p) instead of the whole CTA. Otherwise lines are interleaved thread by
+// thread (padded(e)*P + p) and share __syncthreads.
+template <typename R, int L, int P, int E_ = elems_per_thread(L), bool LM = false>
 struct LineFft {
   static constexpr int E = E_;
   static constexpr int T_LINE = L / E;
   static constexpr int S = num_stages(L, E);
+  static constexpr int SH = pad_shift(E);
+  static constexpr int LS = L + (L >> SH);
   static_assert(L % E == 0, "bad E");
+  static_assert(!LM || (T_LINE % 32 == 0 && P <= 15), "line-major needs whole warps per line");
+
+  static __device__ __forceinline__ void sync(int p) {
+    if constexpr (LM) {
+      asm volatile("bar.sync %0, %1;\n" ::"r"(p + 1), "n"(T_LINE) : "memory");
+    } else {
+      __syncthreads();
+    }
+  }
+  static __device__ __forceinline__ int sidx(int p, int e) {
+    if constexpr (LM) return p * LS + padded_by<SH>(e);
+    return padded_by<SH>(e) * P + p;
+  }
 
   // One Stockham stage; FIRST stage reads the registers, later stages read the
   // shared-memory line; the LAST stage leaves its result in registers.
@@ -233,10 +258,10 @@ struct LineFft {
     constexpr int NB = E / RD;  // butterflies per thread
     static_assert(E % RD == 0, "radix must divide E");
     if constexpr (!FIRST) {
-      __syncthreads();
+      sync(p);
 #pragma unroll
-      for (int s = 0; s < E; ++s) v[s] = sm[padded(t + T_LINE * s) * P + p];
-      if constexpr (!LAST) __syncthreads();
+      for (int s = 0; s < E; ++s) v[s] = sm[sidx(p, t + T_LINE * s)];
+      if constexpr (!LAST) sync(p);
     }
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
@@ -258,7 +283,7 @@ struct LineFft {
       } else {
         const int base = (j / NS) * NS * RD + jm;
 #pragma unroll
-        for (int r = 0; r < RD; ++r) sm[padded(base + r * NS) * P + p] = x[r];
+        for (int r = 0; r < RD; ++r) sm[sidx(p, base + r * NS)] = x[r];
       }
     }
   }
@@ -279,11 +304,223 @@ struct LineFft {
 #pragma unroll
       for (int s = 0; s < E; ++s) v[s].y = -v[s].y;
     }
-    if constexpr (S > 1) __syncthreads();  // the previous user of `sm` is done
+    if constexpr (S > 1) sync(p);  // the previous user of `sm` is done
     stages<0>(v, sm, t, p, tw);
     if (inverse) {
 #pragma unroll
       for (int s = 0; s < E; ++s) v[s].y = -v[s].y;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Split-precision tensor-core DFT-16 (the mixed mode, NSLCT_PREC_SPLIT_F16)
+//
+// A radix-16 Stockham stage applied to 8 butterflies at a time is the complex
+// product D = W X of the 16 x 16 DFT matrix W (W[m][k] = e^{-2 pi i mk/16})
+// with X (16 points x 8 butterflies). In real-block form
+//     Re D = Wr Xr - Wi Xi,   Im D = Wi Xr + Wr Xi,
+// and every real operand is split into FP16 halves, v = v_hi + v_lo, so
+//     A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi      (FP32 accumulation)
+// keeps ~22 significant bits. Each product is one warp-level
+// mma.m16n8k16 (f16 inputs, f32 accumulators): 12 per 8 butterflies.
+// Twiddles between stages stay FP32. The data move through shared memory at
+// every stage (the MMA fragments do not match the one-butterfly-per-thread
+// register layout), so the line visits shared memory S + 1 times instead of
+// S - 1.
+// ---------------------------------------------------------------------------
+template <int R> struct W16c {
+  static constexpr float c = (float)cos2pi(R, 16);
+  static constexpr float s = (float)(-sin2pi(R, 16));
+};
+__constant__ float kW16re[16] = {W16c<0>::c, W16c<1>::c, W16c<2>::c, W16c<3>::c, W16c<4>::c, W16c<5>::c,
+                                 W16c<6>::c, W16c<7>::c, W16c<8>::c, W16c<9>::c, W16c<10>::c, W16c<11>::c,
+                                 W16c<12>::c, W16c<13>::c, W16c<14>::c, W16c<15>::c};
+__constant__ float kW16im[16] = {W16c<0>::s, W16c<1>::s, W16c<2>::s, W16c<3>::s, W16c<4>::s, W16c<5>::s,
+                                 W16c<6>::s, W16c<7>::s, W16c<8>::s, W16c<9>::s, W16c<10>::s, W16c<11>::s,
+                                 W16c<12>::s, W16c<13>::s, W16c<14>::s, W16c<15>::s};
+
+__device__ __forceinline__ uint32_t h2bits(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+// FP16 halves of (a, b): hi = fp16(v), lo = fp16(v - hi), packed low = a
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  hi = h2bits(h);
+  lo = h2bits(__floats2half2_rn(a - hf.x, b - hf.y));
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Constant A fragments of W (row-major 16 x 16) for this lane: register q holds
+// rows g + 8 (q & 1), columns 2c + 8 (q >> 1) + {0, 1}, g = lane / 4, c = lane % 4.
+struct DftFrags {
+  uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4], nim_hi[4], nim_lo[4];
+  __device__ __forceinline__ void init(int lane) {
+    const int g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = g + 8 * (q & 1), k0 = 2 * c + 8 * (q >> 1);
+      const int r0 = (m * k0) & 15, r1 = (m * (k0 + 1)) & 15;
+      split_pair(kW16re[r0], kW16re[r1], re_hi[q], re_lo[q]);
+      split_pair(kW16im[r0], kW16im[r1], im_hi[q], im_lo[q]);
+      split_pair(-kW16im[r0], -kW16im[r1], nim_hi[q], nim_lo[q]);
+    }
+  }
+};
+
+template <int L, int P, int E>
+struct MixedLineFft {
+  using Base = LineFft<float, L, P, E, false>;
+  static constexpr int T_LINE = L / E;
+  static constexpr int S = num_stages(L, E);
+  static constexpr int NBF = L / 16;                   // radix-16 butterflies per line
+  static constexpr int THREADS = T_LINE * P;
+  static_assert(E == 16, "the split-precision mode runs with 16 elements per thread");
+
+  static __device__ __forceinline__ int sidx(int p, int e) { return padded(e) * P + p; }
+
+  // One radix-16 stage on tensor cores, shared memory -> shared memory.
+  template <int ST>
+  static __device__ __forceinline__ void mma_stage(float2* sm, const float2* __restrict__ tw, const DftFrags& W) {
+    constexpr int NS = stage_ns(L, E, ST);
+    constexpr int NG = NBF / 8;                          // 8-butterfly groups per line
+    constexpr int GPW = (P * NG) / (THREADS / 32);       // groups per warp (4)
+    static_assert((P * NG) % (THREADS / 32) == 0, "groups per warp");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, c = lane & 3;
+    uint32_t xr_hi[GPW][2], xr_lo[GPW][2], xi_hi[GPW][2], xi_lo[GPW][2];
+    float inv_scale[GPW];  // 2^e of the butterfly this lane fed in (vector g)
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GPW; ++q) {
+      const int G = warp * GPW + q;
+      const int p = G / NG, j = (G % NG) * 8 + g;
+      float2 x[4];
+      const int ks[4] = {2 * c, 2 * c + 1, 2 * c + 8, 2 * c + 9};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = sm[sidx(p, j + ks[u] * NBF)];
+      if constexpr (NS > 1) {
+        const float4* row = reinterpret_cast<const float4*>(tw + stage_table_offset(L, E, ST) + (j % NS) * 16);
+        const float4 w01 = __ldg(row + c), w89 = __ldg(row + c + 4);
+        x[0] = cmul<float>(x[0], make_float2(w01.x, w01.y));
+        x[1] = cmul<float>(x[1], make_float2(w01.z, w01.w));
+        x[2] = cmul<float>(x[2], make_float2(w89.x, w89.y));
+        x[3] = cmul<float>(x[3], make_float2(w89.z, w89.w));
+      }
+      // Scale the butterfly (held by the 4 lanes with this g) by an exact power
+      // of two so its largest component lies in [0.5, 1): FP16 neither
+      // overflows (unnormalised FFT values grow to ~N |x|) nor drops the small
+      // split halves into subnormals.
+      float mx = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mx = fmaxf(mx, fmaxf(fabsf(x[u].x), fabsf(x[u].y)));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      // clamped so that both 2^-ex and 2^ex stay finite: subnormal inputs (the
+      // underflowed tails of a field) would otherwise ask for 2^+132
+      const int ex = mx > 0.f ? min(max(ilogbf(mx) + 1, -125), 127) : 0;
+      const float sc = ldexpf(1.0f, -ex);
+      inv_scale[q] = ldexpf(1.0f, ex);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = make_float2(x[u].x * sc, x[u].y * sc);
+      split_pair(x[0].x, x[1].x, xr_hi[q][0], xr_lo[q][0]);
+      split_pair(x[2].x, x[3].x, xr_hi[q][1], xr_lo[q][1]);
+      split_pair(x[0].y, x[1].y, xi_hi[q][0], xi_lo[q][0]);
+      split_pair(x[2].y, x[3].y, xi_hi[q][1], xi_lo[q][1]);
+    }
+    __syncthreads();  // every input read before any output lands
+#pragma unroll
+    for (int q = 0; q < GPW; ++q) {
+      const int G = warp * GPW + q;
+      const int p = G / NG, gbase = (G % NG) * 8;
+      float dr[4] = {0.f, 0.f, 0.f, 0.f}, di[4] = {0.f, 0.f, 0.f, 0.f};
+      mma16816(dr, W.re_hi, xr_hi[q][0], xr_hi[q][1]);
+      mma16816(dr, W.re_hi, xr_lo[q][0], xr_lo[q][1]);
+      mma16816(dr, W.re_lo, xr_hi[q][0], xr_hi[q][1]);
+      mma16816(dr, W.nim_hi, xi_hi[q][0], xi_hi[q][1]);
+      mma16816(dr, W.nim_hi, xi_lo[q][0], xi_lo[q][1]);
+      mma16816(dr, W.nim_lo, xi_hi[q][0], xi_hi[q][1]);
+      mma16816(di, W.im_hi, xr_hi[q][0], xr_hi[q][1]);
+      mma16816(di, W.im_hi, xr_lo[q][0], xr_lo[q][1]);
+      mma16816(di, W.im_lo, xr_hi[q][0], xr_hi[q][1]);
+      mma16816(di, W.re_hi, xi_hi[q][0], xi_hi[q][1]);
+      mma16816(di, W.re_hi, xi_lo[q][0], xi_lo[q][1]);
+      mma16816(di, W.re_lo, xi_hi[q][0], xi_hi[q][1]);
+      // d[v]: output point m = g + 8 (v >> 1) of butterfly (vector) n = 2c + (v & 1),
+      // whose scale sits with the lanes 4n .. 4n + 3
+      const float us0 = __shfl_sync(0xffffffffu, inv_scale[q], 8 * c);
+      const float us1 = __shfl_sync(0xffffffffu, inv_scale[q], 8 * c + 4);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int m = g + 8 * (v >> 1);
+        const int j = gbase + 2 * c + (v & 1);
+        const int base = (j / NS) * NS * 16 + (j % NS);
+        const float us = (v & 1) ? us1 : us0;
+        sm[sidx(p, base + m * NS)] = make_float2(dr[v] * us, di[v] * us);
+      }
+    }
+  }
+
+  // A non-radix-16 stage, FP32, shared memory -> shared memory.
+  template <int ST>
+  static __device__ __forceinline__ void fp32_stage(float2* sm, const float2* __restrict__ tw, int t, int p) {
+    constexpr int RD = stage_radix(L, E, ST);
+    constexpr int NS = stage_ns(L, E, ST);
+    constexpr int NB = E / RD;
+    float2 v[E];
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = sm[sidx(p, t + T_LINE * s)];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      float2 x[RD];
+#pragma unroll
+      for (int r = 0; r < RD; ++r) x[r] = v[u + r * NB];
+      const int j = t + u * T_LINE;
+      const int jm = j % NS;
+      if constexpr (NS > 1) {
+        float2 w[RD];
+        load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+#pragma unroll
+        for (int r = 1; r < RD; ++r) x[r] = cmul<float>(x[r], w[r]);
+      }
+      Dft<float, RD>::run(x);
+      const int base = (j / NS) * NS * RD + jm;
+#pragma unroll
+      for (int r = 0; r < RD; ++r) sm[sidx(p, base + r * NS)] = x[r];
+    }
+  }
+
+  template <int ST>
+  static __device__ __forceinline__ void stages(float2* sm, const float2* __restrict__ tw, int t, int p,
+                                                const DftFrags& W) {
+    if constexpr (ST < S) {
+      if constexpr (stage_radix(L, E, ST) == 16) mma_stage<ST>(sm, tw, W);
+      else fp32_stage<ST>(sm, tw, t, p);
+      stages<ST + 1>(sm, tw, t, p, W);
+    }
+  }
+
+  static __device__ __forceinline__ void run(float2* v, float2* sm, int t, int p, const float2* __restrict__ tw,
+                                             bool inverse) {
+    DftFrags W;
+    W.init(threadIdx.x & 31);
+    __syncthreads();  // the previous user of `sm` is done
+#pragma unroll
+    for (int s = 0; s < E; ++s) sm[sidx(p, t + T_LINE * s)] = make_float2(v[s].x, inverse ? -v[s].y : v[s].y);
+    stages<0>(sm, tw, t, p, W);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const float2 z = sm[sidx(p, t + T_LINE * s)];
+      v[s] = make_float2(z.x, inverse ? -z.y : z.y);
     }
   }
 };
@@ -326,12 +563,22 @@ __device__ __forceinline__ int elem_index(int i, int j, int Ny, int tiled) {
 // T_LINE). So the Q0.64 phase is advanced with two 64-bit additions per
 // element: q(s+1) = q(s) + D(s), D(s+1) = D(s) + 2 k T^2, all exact mod 2^64.
 template <typename R, int L, bool COL, int E = elems_per_thread(L)>
+__device__ __forceinline__ void apply_chirp_c(cpx<R>* v, const PassDesc& d, const Chirp& ch, int freq, int t,
+                                              int line, R scale);
+
+template <typename R, int L, bool COL, int E = elems_per_thread(L)>
 __device__ __forceinline__ void apply_chirp(cpx<R>* v, const PassDesc& d, int t, int line, R scale) {
+  apply_chirp_c<R, L, COL, E>(v, d, d.chirp, d.freq_domain, t, line, scale);
+}
+
+template <typename R, int L, bool COL, int E>
+__device__ __forceinline__ void apply_chirp_c(cpx<R>* v, const PassDesc& d, const Chirp& ch, int freq, int t,
+                                              int line, R scale) {
   constexpr int T = L / E;
   const int nl = COL ? d.Ny : d.Nx;   // length of the other axis
   // coordinate of the line and of element 0
   long long b, a0;
-  if (d.freq_domain) {
+  if (freq) {
     b = centred_bin(line, nl);
     a0 = t;
   } else {
@@ -339,9 +586,9 @@ __device__ __forceinline__ void apply_chirp(cpx<R>* v, const PassDesc& d, int t,
     a0 = (long long)t - L / 2;
   }
   // phase = ka a^2 + kab a b + kb b^2 with (ka, kb) the element/line coefficients
-  const uint64_t ka = COL ? d.chirp.k11 : d.chirp.k22;
-  const uint64_t kb = COL ? d.chirp.k22 : d.chirp.k11;
-  const uint64_t kab_b = d.chirp.k12 * (uint64_t)b;
+  const uint64_t ka = COL ? ch.k11 : ch.k22;
+  const uint64_t kb = COL ? ch.k22 : ch.k11;
+  const uint64_t kab_b = ch.k12 * (uint64_t)b;
   const uint64_t base = kb * (uint64_t)(b * b);
   auto phase_at = [&](long long a) -> uint64_t { return ka * (uint64_t)(a * a) + kab_b * (uint64_t)a + base; };
   const uint64_t dd = 2ull * ka * (uint64_t)((long long)T * T);
@@ -349,7 +596,7 @@ __device__ __forceinline__ void apply_chirp(cpx<R>* v, const PassDesc& d, int t,
   uint64_t dq = ka * (uint64_t)(2 * a0 * T + (long long)T * T) + kab_b * (uint64_t)T;
 #pragma unroll
   for (int s = 0; s < E; ++s) {
-    if (d.freq_domain && s == E / 2) {
+    if (freq && s == E / 2) {
       const long long a = a0 + (long long)T * s - L;
       q = phase_at(a);
       dq = ka * (uint64_t)(2 * a * T + (long long)T * T) + kab_b * (uint64_t)T;
@@ -502,21 +749,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-template <int L, bool COL> struct PShape {
-  static constexpr int E = kernel_elems(L, true);
+template <int L, bool COL, int E_ = kernel_elems(L, true)> struct PShape {
+  static constexpr int E = E_;
   static constexpr int T_LINE = L / E;
   // panel of ~8192 complex per CTA (~4096 for 24-element threads) keeps the
-  // exchange buffer and the two staging buffers within 227 KB of shared memory
-  static constexpr int MAXT = E > 16 ? 256 : (E < 16 ? 1024 : 512);
+  // exchange buffer and the staging buffers within 227 KB of shared memory
+  static constexpr int MAXT = E >= 64 ? 128 : (E > 16 ? 256 : (E < 16 ? 1024 : 512));
   static constexpr int P0 = MAXT / T_LINE;
   static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);
   static constexpr int THREADS = T_LINE * P;
-  static constexpr int XSM = P * (L + L / 16);                   // exchange buffer entries
+  static constexpr int XSM = P * (L + (L >> pad_shift(E)));      // exchange buffer entries
   static constexpr int STG = COL ? P * L : P * (L + 8);          // one staging buffer (row-major rows padded)
-  // column panels leave through an output staging buffer and TMA stores; row
-  // panels are whole contiguous rows and are stored straight from registers
+  // Column panels leave through an output staging buffer and TMA stores; row
+  // panels are whole contiguous rows, stored straight from registers. One
+  // input buffer each: a second one for row passes (two panels in flight) was
+  // measured slower (25.4 vs 26.4 Gsamples/s at 4096^2).
+  static constexpr int NIN = 1;
   static constexpr int NSTG = COL ? 2 : 1;
-  static constexpr size_t SMEM = (size_t)(XSM + NSTG * STG) * sizeof(float2) + 16;
+  static constexpr size_t SMEM = (size_t)(XSM + NSTG * STG) * sizeof(float2) + 64;
   static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
   // TMA boxes start on 128-byte boundaries of shared memory
   static_assert((XSM * sizeof(float2)) % 128 == 0 && (STG * sizeof(float2)) % 128 == 0, "staging alignment");
@@ -538,10 +788,9 @@ __device__ __forceinline__ int stg_index(int p, int e, int tiled) {
 }
 
 // Thread 0: start the copies of one panel into `stg`, arming the mbarrier.
-template <int L, bool COL>
+template <int L, bool COL, int P>
 __device__ __forceinline__ void tma_load_panel(float2* stg, const float2* in, const CUtensorMap* map,
                                                const PassDesc& d, int panel, uint64_t* bar) {
-  constexpr int P = PShape<L, COL>::P;
   const int first = panel * P;
   if (COL) {
     const int rows = d.Nx >> 1;                      // row pairs
@@ -562,10 +811,9 @@ __device__ __forceinline__ void tma_load_panel(float2* stg, const float2* in, co
 }
 
 // Thread 0: send one finished panel from `stg` to global memory.
-template <int L, bool COL>
+template <int L, bool COL, int P>
 __device__ __forceinline__ void tma_store_panel(const float2* stg, float2* out, const CUtensorMap* map,
                                                 const PassDesc& d, int panel) {
-  constexpr int P = PShape<L, COL>::P;
   const int first = panel * P;
   if (COL) {
     const int rows = d.Nx >> 1;
@@ -583,23 +831,28 @@ __device__ __forceinline__ void tma_store_panel(const float2* stg, float2* out, 
   bulk_commit();
 }
 
-template <int L, bool COL>
-__global__ void __launch_bounds__(PShape<L, COL>::THREADS, 1)
+template <int L, bool COL, bool MIXED = false>
+__global__ void __launch_bounds__(PShape<L, COL, MIXED ? elems_per_thread(L) : kernel_elems(L, true)>::THREADS, 1)
 pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out) {
-  using Sh = PShape<L, COL>;
+  using Sh = PShape<L, COL, MIXED ? elems_per_thread(L) : kernel_elems(L, true)>;
   constexpr int E = Sh::E;
   constexpr int T_LINE = Sh::T_LINE;
   constexpr int P = Sh::P;
+  // Line-major threads with per-line named barriers were measured slower
+  // (18.9 vs 26.4 Gsamples/s at 4096^2): lines stay interleaved per thread.
+  constexpr bool LM = false;
+  using Fft = typename std::conditional<MIXED, MixedLineFft<L, P, E>, LineFft<float, L, P, E, LM>>::type;
+  constexpr int NIN = Sh::NIN;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* xs = reinterpret_cast<float2*>(smem_raw);
-  float2* stg_in = xs + Sh::XSM;
-  float2* stg_out = stg_in + Sh::STG;  // only for column passes
-  uint64_t* bar = reinterpret_cast<uint64_t*>(stg_in + Sh::NSTG * Sh::STG);
-  volatile int& s_ok = *reinterpret_cast<volatile int*>(bar + 1);
+  float2* stg_in = xs + Sh::XSM;                     // NIN input buffers of STG entries
+  float2* stg_out = stg_in + Sh::STG;                 // column passes: the output buffer
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stg_in + Sh::NSTG * Sh::STG);  // one per input buffer
+  volatile int& s_ok = *reinterpret_cast<volatile int*>(bar + NIN);
 
   const int tid = threadIdx.x;
-  const int p = tid % P;
-  const int t = tid / P;
+  const int p = LM ? tid / T_LINE : tid % P;
+  const int t = LM ? tid % T_LINE : tid / P;
   const int nlines = COL ? d.Ny : d.Nx;
   const int npanels = (nlines + P - 1) / P;
   const float2* in = reinterpret_cast<const float2*>(d.in);
@@ -607,56 +860,67 @@ pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   const float scale = d.fscale;
 
-  int panel = blockIdx.x;
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int b = 0; b < NIN; ++b) mbar_init(bar + b, 1);
     mbar_fence_init();
-    if (panel < npanels) tma_load_panel<L, COL>(stg_in, in, &map_in, d, panel, bar);
+    for (int b = 0; b < NIN; ++b) {
+      const int pb = blockIdx.x + b * gridDim.x;
+      if (pb < npanels) tma_load_panel<L, COL, P>(stg_in + b * Sh::STG, in, &map_in, d, pb, bar + b);
+    }
   }
   __syncthreads();
-  uint32_t parity = 0;
-  for (; panel < npanels; panel += gridDim.x) {
+  int it = 0;
+  for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x, ++it) {
     const int line = panel * P + p;
     const bool valid = line < nlines;
+    const int b = NIN == 1 ? 0 : (it % NIN);
+    const uint32_t parity = (uint32_t)((it / NIN) & 1);
+    float2* buf = stg_in + b * Sh::STG;
     if (tid == 0) {
-      s_ok = mbar_wait_bounded(bar, parity) ? 1 : 0;
+      s_ok = mbar_wait_bounded(bar + b, parity) ? 1 : 0;
       if (COL) bulk_wait_read_all();  // the previous panel's stores have left stg_out
     }
     __syncthreads();
     if (!s_ok) {
       if (tid == 0) {
         if (d.err) atomicOr(d.err, 1u);
-        mbar_wait_bounded(bar, parity);  // give the copy in flight one more bounded chance
+        for (int k = 0; k < NIN; ++k) mbar_wait_bounded(bar + k, (uint32_t)(((it + k) / NIN) & 1));
         bulk_wait_all();
       }
       return;
     }
-    parity ^= 1u;
     float2 v[E];
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = stg_in[stg_index<L, COL, P>(p, t + T_LINE * s, d.in_tiled)];
-    __syncthreads();  // stg_in consumed
-    const int next = panel + gridDim.x;
+    for (int s = 0; s < E; ++s) v[s] = buf[stg_index<L, COL, P>(p, t + T_LINE * s, d.in_tiled)];
+    __syncthreads();  // this input buffer is consumed
+    const int next = panel + NIN * gridDim.x;
     if (tid == 0 && next < npanels) {
       fence_proxy_async();
-      tma_load_panel<L, COL>(stg_in, in, &map_in, d, next, bar);
+      tma_load_panel<L, COL, P>(buf, in, &map_in, d, next, bar + b);
     }
 
-    if (d.t1 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t1 == kInv);
+    if (d.t1 != kNone) Fft::run(v, xs, t, p, tw, d.t1 == kInv);
     if (d.has_chirp) {
       apply_chirp<float, L, COL, E>(v, d, t, line, scale);
     } else if (d.scale_only) {
 #pragma unroll
       for (int s = 0; s < E; ++s) v[s] = make_float2(v[s].x * scale, v[s].y * scale);
     }
-    if (d.t2 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t2 == kInv);
+    if (d.t2 != kNone) Fft::run(v, xs, t, p, tw, d.t2 == kInv);
+    if (d.has_chirp2) {
+      apply_chirp_c<float, L, COL, E>(v, d, d.chirp2, d.freq_domain2, t, line, d.fscale2);
+    } else if (d.fscale2 != 1.0f) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = make_float2(v[s].x * d.fscale2, v[s].y * d.fscale2);
+    }
+    if (d.t3 != kNone) Fft::run(v, xs, t, p, tw, d.t3 == kInv);
 
     if constexpr (COL) {
 #pragma unroll
       for (int s = 0; s < E; ++s) stg_out[stg_index<L, COL, P>(p, t + T_LINE * s, 1)] = v[s];
       fence_proxy_async();
       __syncthreads();
-      if (tid == 0) tma_store_panel<L, COL>(stg_out, out, &map_out, d, panel);
+      if (tid == 0) tma_store_panel<L, COL, P>(stg_out, out, &map_out, d, panel);
     } else if (valid) {
 #pragma unroll
       for (int s = 0; s < E; ++s) out[elem_index(line, t + T_LINE * s, d.Ny, d.out_tiled)] = v[s];
@@ -670,18 +934,337 @@ pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __
 // tiles) and up to 256 row pairs tall. Complex64 values are 8-byte elements.
 bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P);
 
+// ---------------------------------------------------------------------------
+// v4 (FP32, power-of-two lines of 256..4096): line-pair kernel.
+//
+// A CTA of 256 threads owns G = 256 / (L/16) line PAIRS (a row pair, or a
+// column pair: the unit of the 2x2-tiled layout); thread t of a pair holds the
+// elements e = t + (L/16) s, s < 16, of BOTH lines. So
+//   * every shared-memory exchange of a Stockham stage moves (line0[e], line1[e])
+//     as one 16-byte access instead of two 8-byte ones, and each twiddle load
+//     serves both lines;
+//   * a column pair's TMA box lands as exactly that layout (per row pair the
+//     tile holds line0[2r], line1[2r], line0[2r+1], line1[2r+1]), and leaves
+//     from it.
+// The panel lands by TMA in the exchange buffer itself (no separate staging
+// buffer): one CTA needs ~70 KB of shared memory and 128 registers a thread,
+// so two CTAs share an SM and overlap each other's loads, stores and barriers.
+// Waits are bounded as in v3.
+// ---------------------------------------------------------------------------
+template <int L> struct PairShape {
+  static constexpr int E = 16;
+  static constexpr int T = L / E;                 // threads per line pair
+  static constexpr int THREADS = 256;
+  static constexpr int G = THREADS / T;           // line pairs per CTA
+  static constexpr int P = 2 * G;                 // lines per CTA
+  static constexpr int SH = pad_shift(E);
+  static constexpr int LS = L + (L >> SH);        // float4 entries per pair region (padded)
+  static constexpr size_t SMEM = (size_t)G * LS * sizeof(float4) + 64;
+  static_assert(is_pow2(L) && L >= 256 && L <= 4096, "pair kernel lengths");
+  static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
+  static_assert((LS * sizeof(float4)) % 128 == 0, "TMA destinations on 128-byte boundaries");
+  static_assert(2 * (L + 8) <= 2 * LS, "row landing fits the pair region");
+};
+
+template <int L> struct PairFft {
+  using Sh = PairShape<L>;
+  static constexpr int E = Sh::E;
+  static constexpr int T = Sh::T;
+  static constexpr int S = num_stages(L, E);
+  static constexpr int SH = Sh::SH;
+
+  static __device__ __forceinline__ int sidx(int g, int e) { return g * Sh::LS + padded_by<SH>(e); }
+
+  template <int ST>
+  static __device__ __forceinline__ void stage(float2* v0, float2* v1, float4* sm, int t, int g,
+                                               const float2* __restrict__ tw) {
+    constexpr int RD = stage_radix(L, E, ST);
+    constexpr int NS = stage_ns(L, E, ST);
+    constexpr bool FIRST = (ST == 0);
+    constexpr bool LAST = (ST == S - 1);
+    constexpr int NB = E / RD;
+    static_assert(E % RD == 0, "radix must divide E");
+    if constexpr (!FIRST) {
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const float4 q = sm[sidx(g, t + T * s)];
+        v0[s] = make_float2(q.x, q.y);
+        v1[s] = make_float2(q.z, q.w);
+      }
+      if constexpr (!LAST) __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      float2 x0[RD], x1[RD];
+#pragma unroll
+      for (int r = 0; r < RD; ++r) {
+        x0[r] = v0[u + r * NB];
+        x1[r] = v1[u + r * NB];
+      }
+      const int j = t + u * T;
+      const int jm = j % NS;
+      if constexpr (NS > 1) {
+        float2 w[RD];
+        load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+#pragma unroll
+        for (int r = 1; r < RD; ++r) {
+          x0[r] = cmul<float>(x0[r], w[r]);
+          x1[r] = cmul<float>(x1[r], w[r]);
+        }
+      }
+      Dft<float, RD>::run(x0);
+      Dft<float, RD>::run(x1);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < RD; ++r) {
+          v0[u + r * NB] = x0[r];
+          v1[u + r * NB] = x1[r];
+        }
+      } else {
+        const int base = (j / NS) * NS * RD + jm;
+#pragma unroll
+        for (int r = 0; r < RD; ++r)
+          sm[sidx(g, base + r * NS)] = make_float4(x0[r].x, x0[r].y, x1[r].x, x1[r].y);
+      }
+    }
+  }
+
+  template <int ST>
+  static __device__ __forceinline__ void stages(float2* v0, float2* v1, float4* sm, int t, int g,
+                                                const float2* __restrict__ tw) {
+    if constexpr (ST < S) {
+      stage<ST>(v0, v1, sm, t, g, tw);
+      stages<ST + 1>(v0, v1, sm, t, g, tw);
+    }
+  }
+
+  // Unnormalised DFT (or inverse, as conj(DFT(conj x))) of both lines.
+  static __device__ __forceinline__ void run(float2* v0, float2* v1, float4* sm, int t, int g,
+                                             const float2* __restrict__ tw, bool inverse) {
+    if (inverse) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        v0[s].y = -v0[s].y;
+        v1[s].y = -v1[s].y;
+      }
+    }
+    __syncthreads();  // the previous user of `sm` is done
+    stages<0>(v0, v1, sm, t, g, tw);
+    if (inverse) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        v0[s].y = -v0[s].y;
+        v1[s].y = -v1[s].y;
+      }
+    }
+  }
+};
+
+// Thread 0: copies of one panel (G line pairs from line `first`) into the
+// pair regions of `x`, arming the mbarrier. Column pairs: one 2D box column
+// (4 complex wide) per pair; row pairs: one or two 1D bulk copies per pair.
+template <int L, bool COL>
+__device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, const CUtensorMap* map,
+                                                const PassDesc& d, int first, uint64_t* bar) {
+  using Sh = PairShape<L>;
+  const int nlines = COL ? d.Ny : d.Nx;
+  const int pairs = min(Sh::G, (nlines - first) >> 1);
+  if (COL) {
+    const int rows = d.Nx >> 1;
+    const int box = col_box_rows(rows);
+    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * rows * 4 * sizeof(float2)));
+    for (int g = 0; g < pairs; ++g)
+      for (int y0 = 0; y0 < rows; y0 += box)
+        tma_load_2d(reinterpret_cast<float2*>(x + g * Sh::LS) + y0 * 4, map, 2 * (first + 2 * g), y0, bar);
+  } else if (d.in_tiled) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)));
+    for (int g = 0; g < pairs; ++g)
+      bulk_load(x + g * Sh::LS, in + (size_t)((first >> 1) + g) * (2 * L), 2 * L * sizeof(float2), bar);
+  } else {
+    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)));
+    for (int g = 0; g < pairs; ++g)
+      for (int h = 0; h < 2; ++h)
+        bulk_load(reinterpret_cast<float2*>(x + g * Sh::LS) + h * (L + 8), in + (size_t)(first + 2 * g + h) * L,
+                  L * sizeof(float2), bar);
+  }
+}
+
+template <int L, bool COL>
+__global__ void __launch_bounds__(256, 2)
+pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out) {
+  using Sh = PairShape<L>;
+  using Fft = PairFft<L>;
+  constexpr int E = Sh::E;
+  constexpr int T = Sh::T;
+  constexpr int P = Sh::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4* xs = reinterpret_cast<float4*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xs + Sh::G * Sh::LS);
+  volatile int& s_ok = *reinterpret_cast<volatile int*>(bar + 1);
+
+  const int tid = threadIdx.x;
+  const int g = tid / T;
+  const int t = tid % T;
+  const int nlines = COL ? d.Ny : d.Nx;
+  const int npanels = (nlines + P - 1) / P;
+  const float2* in = reinterpret_cast<const float2*>(d.in);
+  float2* out = reinterpret_cast<float2*>(d.out);
+  const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
+  float4* xg = xs + g * Sh::LS;                 // this thread's pair region
+  float2* xg2 = reinterpret_cast<float2*>(xg);
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    if ((int)blockIdx.x < npanels) pair_load_panel<L, COL>(xs, in, &map_in, d, blockIdx.x * P, bar);
+  }
+  __syncthreads();
+  int it = 0;
+  for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x, ++it) {
+    const int first = panel * P;
+    const int line0 = first + 2 * g;
+    const bool valid = line0 < nlines;          // lines come in pairs (even counts)
+    if (tid == 0) s_ok = mbar_wait_bounded(bar, (uint32_t)(it & 1)) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {
+      if (tid == 0) {
+        if (d.err) atomicOr(d.err, 1u);
+        bulk_wait_all();
+      }
+      return;
+    }
+    float2 v0[E], v1[E];
+    if (COL) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const float4 q = xg[t + T * s];
+        v0[s] = make_float2(q.x, q.y);
+        v1[s] = make_float2(q.z, q.w);
+      }
+    } else if (d.in_tiled) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const int e = t + T * s;
+        v0[s] = xg2[(e >> 1) * 4 + (e & 1)];
+        v1[s] = xg2[(e >> 1) * 4 + 2 + (e & 1)];
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        v0[s] = xg2[t + T * s];
+        v1[s] = xg2[(L + 8) + t + T * s];
+      }
+    }
+
+    const float scale = d.fscale;
+    if (d.t1 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t1 == kInv);
+    if (d.has_chirp) {
+      apply_chirp_c<float, L, COL, E>(v0, d, d.chirp, d.freq_domain, t, line0, scale);
+      apply_chirp_c<float, L, COL, E>(v1, d, d.chirp, d.freq_domain, t, line0 + 1, scale);
+    } else if (d.scale_only) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        v0[s] = make_float2(v0[s].x * scale, v0[s].y * scale);
+        v1[s] = make_float2(v1[s].x * scale, v1[s].y * scale);
+      }
+    }
+    if (d.t2 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t2 == kInv);
+    if (d.has_chirp2) {
+      apply_chirp_c<float, L, COL, E>(v0, d, d.chirp2, d.freq_domain2, t, line0, d.fscale2);
+      apply_chirp_c<float, L, COL, E>(v1, d, d.chirp2, d.freq_domain2, t, line0 + 1, d.fscale2);
+    } else if (d.fscale2 != 1.0f) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        v0[s] = make_float2(v0[s].x * d.fscale2, v0[s].y * d.fscale2);
+        v1[s] = make_float2(v1[s].x * d.fscale2, v1[s].y * d.fscale2);
+      }
+    }
+    if (d.t3 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t3 == kInv);
+    __syncthreads();  // every thread has finished reading the buffer
+    const int next = panel + gridDim.x;
+
+    if constexpr (COL) {
+      // leave through the buffer: the box layout is (line0[e], line1[e]) per e
+#pragma unroll
+      for (int s = 0; s < E; ++s)
+        xg[t + T * s] = make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        const int pairs = min(Sh::G, (nlines - first) >> 1);
+        const int rows = d.Nx >> 1;
+        const int box = col_box_rows(rows);
+        for (int q = 0; q < pairs; ++q)
+          for (int y0 = 0; y0 < rows; y0 += box)
+            tma_store_2d(&map_out, 2 * (first + 2 * q), y0, reinterpret_cast<float2*>(xs + q * Sh::LS) + y0 * 4);
+        bulk_commit();
+        bulk_wait_read_all();  // the buffer is free again
+        if (next < npanels) pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
+      }
+    } else {
+      if (tid == 0 && next < npanels) {
+        fence_proxy_async();
+        pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
+      }
+      if (valid) {
+        if (d.out_tiled) {
+          float2* o = out + (size_t)(line0 >> 1) * (2 * L);
+#pragma unroll
+          for (int s = 0; s < E; ++s) {
+            const int e = t + T * s;
+            o[(e >> 1) * 4 + (e & 1)] = v0[s];
+            o[(e >> 1) * 4 + 2 + (e & 1)] = v1[s];
+          }
+        } else {
+          float2* o = out + (size_t)line0 * L;
+#pragma unroll
+          for (int s = 0; s < E; ++s) {
+            o[t + T * s] = v0[s];
+            o[L + t + T * s] = v1[s];
+          }
+        }
+      }
+    }
+  }
+  if (COL && tid == 0) bulk_wait_all();
+}
+
+#ifndef NSLCT_PAIR
+#define NSLCT_PAIR 1
+#endif
+
 template <typename R, int L, bool COL>
 inline int launch_one(const PassDesc& d, cudaStream_t s) {
   const int nlines = COL ? d.Ny : d.Nx;
   if constexpr (sizeof(R) == 4) {
+    alignas(64) CUtensorMap mi{}, mo{};
+    if constexpr (is_pow2(L) && L >= 256) {
+      if (d.mixed) {
+        using Sh = PShape<L, COL, elems_per_thread(L)>;
+        const int npanels = (nlines + Sh::P - 1) / Sh::P;
+        const int blocks = npanels < d.num_sms ? npanels : d.num_sms;
+        if (COL && (!encode_column_map(&mi, d.in, d.Nx, d.Ny, Sh::P) ||
+                    !encode_column_map(&mo, d.out, d.Nx, d.Ny, Sh::P)))
+          return NSLCT_E_CUDA;
+        pass_kernel_tma<L, COL, true><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, mi, mo);
+        return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+      }
+    }
+    if constexpr (NSLCT_PAIR && is_pow2(L) && L >= 256) {
+      using Sh = PairShape<L>;
+      const int npanels = (nlines + Sh::P - 1) / Sh::P;
+      const int blocks = npanels < 2 * d.num_sms ? npanels : 2 * d.num_sms;
+      if (COL && (!encode_column_map(&mi, d.in, d.Nx, d.Ny, 2) || !encode_column_map(&mo, d.out, d.Nx, d.Ny, 2)))
+        return NSLCT_E_CUDA;
+      pass_kernel_pair<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, mi, mo);
+      return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+    }
     using Sh = PShape<L, COL>;
     const int npanels = (nlines + Sh::P - 1) / Sh::P;
     const int blocks = npanels < d.num_sms ? npanels : d.num_sms;
-    alignas(64) CUtensorMap mi{}, mo{};
-    if (COL) {
-      if (!encode_column_map(&mi, d.in, d.Nx, d.Ny, Sh::P) || !encode_column_map(&mo, d.out, d.Nx, d.Ny, Sh::P))
-        return NSLCT_E_CUDA;
-    }
+    if (COL && (!encode_column_map(&mi, d.in, d.Nx, d.Ny, Sh::P) || !encode_column_map(&mo, d.out, d.Nx, d.Ny, Sh::P)))
+      return NSLCT_E_CUDA;
     pass_kernel_tma<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, mi, mo);
   } else {
     using Sh = PassShape<R, L>;
@@ -699,6 +1282,22 @@ inline int prepare_one() {
                               (int)PShape<L, false>::SMEM);
     e2 = cudaFuncSetAttribute(pass_kernel_tma<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PShape<L, true>::SMEM);
+    if constexpr (NSLCT_PAIR && is_pow2(L) && L >= 256) {
+      if (e1 == cudaSuccess)
+        e1 = cudaFuncSetAttribute(pass_kernel_pair<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)PairShape<L>::SMEM);
+      if (e2 == cudaSuccess)
+        e2 = cudaFuncSetAttribute(pass_kernel_pair<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)PairShape<L>::SMEM);
+    }
+    if constexpr (is_pow2(L) && L >= 256) {
+      if (e1 == cudaSuccess)
+        e1 = cudaFuncSetAttribute(pass_kernel_tma<L, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)PShape<L, false, elems_per_thread(L)>::SMEM);
+      if (e2 == cudaSuccess)
+        e2 = cudaFuncSetAttribute(pass_kernel_tma<L, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)PShape<L, true, elems_per_thread(L)>::SMEM);
+    }
   } else {
     using Sh = PassShape<R, L>;
     e1 = cudaFuncSetAttribute(pass_kernel<R, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
@@ -723,7 +1322,7 @@ namespace nslct {
 // go to `partials[blockIdx.x][3]` (FP64), reduced later in a fixed order.
 // ---------------------------------------------------------------------------
 template <typename R, int L> struct DualShape {
-  static constexpr int E = kernel_elems(L, sizeof(R) == 4);  // must match the plan's twiddle table
+  static constexpr int E = elems_per_thread(L);  // the plan's tw16 tables
   static constexpr int T_LINE = L / E;
   static constexpr int P0 = 512 / T_LINE;
   static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);

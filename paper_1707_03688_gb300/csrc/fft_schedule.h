@@ -5,9 +5,11 @@ namespace nslct {
 
 __host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// Elements per thread of the FP32 persistent kernels for the largest
-// power-of-two lines (2048, 4096): 8 gives 1024-thread CTAs (radix-8 stages),
-// 16 gives 512-thread CTAs (radix-16 stages). Overridable at build time.
+// Elements per thread of the FP32 forward/inverse kernels for the largest
+// power-of-two lines (2048, 4096): 16 (radix-16 stages, 512-thread CTAs).
+// Measured at 4096^2 (Gsamples/s): 16 -> 26.4, 8 (radix-8, 1024 threads, one
+// more exchange) -> 23.4, 64 (radix-64, 128 threads, one exchange fewer, 255
+// registers) -> 20.6. Overridable at build time.
 #ifndef NSLCT_E_LARGE
 #define NSLCT_E_LARGE 16
 #endif
@@ -16,10 +18,14 @@ __host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)
 __host__ __device__ constexpr int elems_per_thread(int L) {
   return is_pow2(L) ? (L >= 16 ? 16 : L) : (L >= 24 ? 24 : L);
 }
-// elements per thread of the kernel that runs length L (FP32 or FP64)
+// elements per thread of the forward/inverse kernel that runs length L (FP32 or FP64);
+// the adjoint, batched and split-precision kernels use elems_per_thread(L)
 __host__ __device__ constexpr int kernel_elems(int L, bool f32) {
   return (f32 && is_pow2(L) && L >= 2048) ? NSLCT_E_LARGE : elems_per_thread(L);
 }
+// shared-memory padding: one slot per 2^pad_shift elements keeps the
+// stride-E stage writes conflict-free
+__host__ __device__ constexpr int pad_shift(int E) { return E >= 64 ? 6 : 4; }
 // largest power of two <= n that divides e
 __host__ __device__ constexpr int pow2_radix(int n, int e) {
   int r = 1;

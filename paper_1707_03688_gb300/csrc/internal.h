@@ -44,6 +44,13 @@ struct PassDesc {
   int num_sms;         // persistent-grid size for the FP32 kernels
   const void* tw;      // per-stage twiddle table of the pass axis length (see fft_schedule.h)
   unsigned int* err;   // device status word: bit 0 = a bounded wait expired
+  int mixed;           // radix-16 stages as split-FP16 tensor-core DFTs (FP32 data)
+  // optional tail: after t2, a second chirp (x scale2) and a third transform
+  int t3;
+  int has_chirp2;
+  int freq_domain2;
+  Chirp chirp2;
+  float fscale2;       // applied with chirp2 (or alone when != 1)
 };
 
 // Enqueue one pass. `col` selects the axis. Returns an NSLCT_* code.
@@ -66,6 +73,9 @@ int dual_blocks_f64(int L, int nlines);
 // The five pass descriptors of the forward or inverse chain (see api.cpp).
 void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool inverse, PassDesc d[5]);
 bool chain_pass_is_column(int k);
+// The plan's own schedule: 5 passes, or 3 when H acts along y only. Returns
+// the pass count; cols[k] tells the axis of pass k.
+int build_schedule(const nslct_plan_s* p, const void* in, void* out, bool inverse, PassDesc d[5], bool cols[5]);
 
 // True when L is a length the kernels are instantiated for.
 bool supported_length(int L);
@@ -80,6 +90,8 @@ struct nslct_plan_s {
   double dx, dy;
   unsigned flags;
   int prec;            // 0 = fp32, 1 = fp64
+  int mixed;           // NSLCT_PREC_SPLIT_F16: FP32 data, split-FP16 tensor-core DFT-16 stages
+  int y_only_h;        // H = (0,0;0,h): CC^H acts along y only and the chain runs in 3 passes
   int device;
   double M[16];        // the (possibly projected) ABCD matrix
   double H[4], Bp[4], C1[4], C2[4];
@@ -96,6 +108,8 @@ struct nslct_plan_s {
   double* partials;    // backward per-CTA sums (made on first use)
   int partials_stride; // rows per pass in `partials`
   unsigned int* err;   // device status word shared by the plan's kernels
-  void* tw_x;          // device twiddles for length Nx
-  void* tw_y;          // device twiddles for length Ny (may alias tw_x)
+  void* tw_x;          // device twiddles for length Nx, forward/inverse kernels
+  void* tw_y;          // device twiddles for length Ny (tables may alias each other)
+  void* tw16_x;        // twiddles for elems_per_thread(Nx): adjoint and batched kernels
+  void* tw16_y;
 };

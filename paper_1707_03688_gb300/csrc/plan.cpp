@@ -333,6 +333,17 @@ int choose_h_lc(const double* m, Mat2* h_out) {
   return NSLCT_OK;
 }
 
+// Eq. LC10 only: H = (0,0;0,h), h = (b12 - b21)/a12, when a12 != 0 and B' is invertible.
+int choose_h_lc_y(const double* m, Mat2* h_out) {
+  Mat2 a, b, c, d;
+  split_blocks(m, a, b, c, d);
+  if (!(std::fabs(a.m01) > 1e-12)) return NSLCT_E_INFEASIBLE;
+  const Mat2 h = {0, 0, 0, (b.m01 - b.m10) / a.m01};
+  if (!std::isfinite(ha_objective(m, h))) return NSLCT_E_INFEASIBLE;
+  *h_out = h;
+  return NSLCT_OK;
+}
+
 // ---------------------------------------------------------------- fixed-point chirps
 
 // fractional part of x as a Q0.64 fraction of a turn

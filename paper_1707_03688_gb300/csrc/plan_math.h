@@ -40,6 +40,7 @@ double gamma_ratio(const Mat2& c);
 double ha_objective(const double* m, const Mat2& h);
 int choose_h_ha(const double* m, Mat2* h_out);
 int choose_h_lc(const double* m, Mat2* h_out);
+int choose_h_lc_y(const double* m, Mat2* h_out);
 uint64_t turns_q64(double x);
 Chirp chirp_from(const Mat2& c, double da, double db);
 void fill_chirps(nslct_plan_s* p);

@@ -30,17 +30,21 @@ NSLCT_E_UNSUPPORTED = 8
 NSLCT_H_HA = 0x0
 NSLCT_H_LC = 0x1
 NSLCT_H_USER = 0x2
+NSLCT_H_LC_Y = 0x3
+NSLCT_FULL_CHAIN = 0x20
 NSLCT_PROJECT_SP4 = 0x10
 NSLCT_PREC_FP32 = 0x000
 NSLCT_PREC_FP64 = 0x100
+NSLCT_PREC_SPLIT_F16 = 0x200
 
 # every symbol include/nslct.h declares, in declaration order
 EXPORTED = (
     "nslct_plan", "nslct_plan_ex", "nslct_derive", "nslct_plan_params", "nslct_plan_info",
-    "nslct_forward", "nslct_inverse", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
+    "nslct_forward", "nslct_inverse", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
-    "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_forward_each", "nslct_batch_destroy",
+    "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
+    "nslct_batch_tune", "nslct_batch_forward_each", "nslct_batch_destroy",
     "nslct_status", "nslct_destroy", "nslct_strerror", "nslct_version",
 )
 
@@ -83,6 +87,7 @@ def load(path: str | None = None):
                                            ctypes.POINTER(ctypes.c_uint), _PD]),
         "nslct_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+        "nslct_plan_passes": (ctypes.c_int, [_VP]),
         "nslct_forward_pass": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
         "nslct_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "nslct_backward_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -97,6 +102,10 @@ def load(path: str | None = None):
         "nslct_batch_forward": (ctypes.c_int, [_VP, _VP]),
         "nslct_batch_capture": (ctypes.c_int, [_VP, _VP]),
         "nslct_batch_forward_each": (ctypes.c_int, [_VP, _VP]),
+        "nslct_batch_set_split": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "nslct_batch_get_split": (ctypes.c_int, [_VP]),
+        "nslct_batch_tune": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_float)]),
         "nslct_batch_destroy": (ctypes.c_int, [_VP]),
         "nslct_status": (ctypes.c_int, [_VP]),
         "nslct_destroy": (ctypes.c_int, [_VP]),
@@ -291,21 +300,27 @@ class Plan:
     """
 
     def __init__(self, abcd, nx: int, ny: int, dx: float | None = None, dy: float | None = None,
-                 method: str = "ha", h=None, project: bool = False, precision: str = "fp32"):
+                 method: str = "ha", h=None, project: bool = False, precision: str = "fp32",
+                 full_chain: bool = False):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         self.dx = float(dx) if dx is not None else math.sqrt(2 * math.pi / self.nx)
         self.dy = float(dy) if dy is not None else math.sqrt(2 * math.pi / self.ny)
-        flags = {"ha": NSLCT_H_HA, "lc": NSLCT_H_LC}[method] if h is None else NSLCT_H_USER
+        flags = {"ha": NSLCT_H_HA, "lc": NSLCT_H_LC, "lc_y": NSLCT_H_LC_Y}[method] if h is None else NSLCT_H_USER
         if project:
             flags |= NSLCT_PROJECT_SP4
+        if full_chain:
+            flags |= NSLCT_FULL_CHAIN
         if precision == "fp64":
             flags |= NSLCT_PREC_FP64
             self.dtype = torch.complex128
         elif precision == "fp32":
             self.dtype = torch.complex64
+        elif precision == "mixed":
+            flags |= NSLCT_PREC_SPLIT_F16
+            self.dtype = torch.complex64
         else:
-            raise ValueError("precision must be 'fp32' or 'fp64'")
+            raise ValueError("precision must be 'fp32', 'mixed' or 'fp64'")
         self.device = torch.cuda.current_device()
         self.flags = flags
         self.handle = None
@@ -345,6 +360,9 @@ class Plan:
         gch = torch.zeros(12, dtype=torch.float64, device=grad_out.device) if want_chirp else None
         nslct_backward(self.handle, grad_out, y, grad_in, gth, gch, workspace, stream)
         return grad_in, gth, gch
+
+    def passes(self) -> int:
+        return int(load().nslct_plan_passes(_VP(self.handle)))
 
     def params(self):
         return nslct_plan_params(self.handle)
@@ -440,6 +458,22 @@ class Batch:
         import torch
         _check(load().nslct_batch_forward(_VP(self.handle), _stream_ptr(stream, torch.cuda.current_device())),
                "nslct_batch_forward")
+
+    def set_split(self, split: int):
+        """Fields with max(Nx, Ny) >= split run through their own fused passes."""
+        _check(load().nslct_batch_set_split(_VP(self.handle), int(split)), "nslct_batch_set_split")
+
+    @property
+    def split(self) -> int:
+        return int(load().nslct_batch_get_split(_VP(self.handle)))
+
+    def tune(self, stream=None, iters: int = 3):
+        """Autotune the split on the bound buffers; returns (split, ms per forward)."""
+        import torch
+        chosen, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+        _check(load().nslct_batch_tune(_VP(self.handle), _stream_ptr(stream, torch.cuda.current_device()),
+                                       int(iters), ctypes.byref(chosen), ctypes.byref(ms)), "nslct_batch_tune")
+        return chosen.value, ms.value
 
     def forward_each(self, stream=None):
         import torch

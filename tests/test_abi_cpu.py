@@ -73,6 +73,11 @@ def test_derive_lc_closed_form(lib):
         hl = O.lc_h(m)
         assert hl is not None
         np.testing.assert_allclose(d["H"], hl, atol=1e-12)
+        dy = N.nslct_derive(m, flags=N.NSLCT_H_LC_Y)
+        hy = O.lc_h(m, only_y=True)
+        if hy is not None:
+            np.testing.assert_allclose(dy["H"], hy, atol=1e-12)
+            assert dy["H"][0, 0] == 0.0 and dy["H"][0, 1] == 0.0 and dy["H"][1, 0] == 0.0
 
 
 def test_derive_projection_matches_oracle(lib):
