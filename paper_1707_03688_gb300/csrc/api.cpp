@@ -48,6 +48,12 @@ int upload_twiddles(int L, int E, void** dev) {
         host[off + jm * rd + r].x = (R)std::cos(a);
         host[off + jm * rd + r].y = (R)(-std::sin(a));
       }
+    const int coff = compact_table_offset(L, E, st);
+    for (int jm = 0; jm < ns; ++jm) {
+      const double a = kTwoPi * (double)jm / ((double)ns * rd);
+      host[coff + jm].x = (R)std::cos(a);
+      host[coff + jm].y = (R)(-std::sin(a));
+    }
   }
   if (cudaMalloc(dev, sizeof(C2) * n) != cudaSuccess) { *dev = nullptr; return NSLCT_E_NOMEM; }
   if (cudaMemcpy(*dev, host.data(), sizeof(C2) * n, cudaMemcpyHostToDevice) != cudaSuccess) {

@@ -951,6 +951,14 @@ bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P
 // so two CTAs share an SM and overlap each other's loads, stores and barriers.
 // Waits are bounded as in v3.
 // ---------------------------------------------------------------------------
+#ifndef NSLCT_PAIR
+#define NSLCT_PAIR 1
+#endif
+// row passes of the pair kernel: 16-byte tiled loads and stores with a lane-pair shuffle
+#ifndef NSLCT_PAIR_SHFL
+#define NSLCT_PAIR_SHFL 1
+#endif
+
 template <int L> struct PairShape {
   static constexpr int E = 16;
   static constexpr int T = L / E;                 // threads per line pair
@@ -965,6 +973,19 @@ template <int L> struct PairShape {
   static_assert((LS * sizeof(float4)) % 128 == 0, "TMA destinations on 128-byte boundaries");
   static_assert(2 * (L + 8) <= 2 * LS, "row landing fits the pair region");
 };
+
+// w[r] = w1^r for r = 1 .. RD-1 (w[0] unused), each as w[2^k] * w[r - 2^k] with
+// w[2^k] by repeated squaring: at most four roundings deep for RD = 16.
+template <int RD>
+__device__ __forceinline__ void twiddle_powers(float2 w1, float2* w) {
+  w[1] = w1;
+#pragma unroll
+  for (int r = 2; r < RD; ++r) {
+    const int hi = (r & (r - 1)) == 0 ? r / 2 : (1 << (31 - __clz(r)));
+    const int lo = (r & (r - 1)) == 0 ? r / 2 : r - hi;
+    w[r] = cmul<float>(w[hi], w[lo]);
+  }
+}
 
 template <int L> struct PairFft {
   using Sh = PairShape<L>;
@@ -1005,8 +1026,9 @@ template <int L> struct PairFft {
       const int j = t + u * T;
       const int jm = j % NS;
       if constexpr (NS > 1) {
+        // one coalesced load of the base twiddle; its powers in registers
         float2 w[RD];
-        load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+        twiddle_powers<RD>(__ldg(tw + compact_table_offset(L, E, ST) + jm), w);
 #pragma unroll
         for (int r = 1; r < RD; ++r) {
           x0[r] = cmul<float>(x0[r], w[r]);
@@ -1143,11 +1165,27 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         v1[s] = make_float2(q.z, q.w);
       }
     } else if (d.in_tiled) {
+      if constexpr (NSLCT_PAIR_SHFL) {
+        // float4 e of a tiled row pair is (line0[e], line0[e+1]) for even e and
+        // (line1[e-1], line1[e]) for odd e: one 16-byte load per lane, then
+        // lanes e and e^1 swap the half the other one needs
+        const bool odd = (t & 1) != 0;
 #pragma unroll
-      for (int s = 0; s < E; ++s) {
-        const int e = t + T * s;
-        v0[s] = xg2[(e >> 1) * 4 + (e & 1)];
-        v1[s] = xg2[(e >> 1) * 4 + 2 + (e & 1)];
+        for (int s = 0; s < E; ++s) {
+          const float4 q = xg[t + T * s];
+          const float2 mine = odd ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+          const float2 give = odd ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
+          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, give.x, 1), __shfl_xor_sync(0xffffffffu, give.y, 1));
+          v0[s] = odd ? got : mine;
+          v1[s] = odd ? mine : got;
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          const int e = t + T * s;
+          v0[s] = xg2[(e >> 1) * 4 + (e & 1)];
+          v1[s] = xg2[(e >> 1) * 4 + 2 + (e & 1)];
+        }
       }
     } else {
 #pragma unroll
@@ -1207,7 +1245,24 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         fence_proxy_async();
         pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
       }
-      if (valid) {
+      if constexpr (NSLCT_PAIR_SHFL) {
+        // lanes e (even) and e^1 swap halves so that each lane stores one
+        // 16-byte vector: tiled, float4 e; row-major, (line0[e], line0[e+1])
+        // from the even lane and (line1[e-1], line1[e]) from the odd one
+        // (every lane shuffles: with 16 threads per pair a warp can straddle
+        // a valid and an invalid pair)
+        const bool odd = (t & 1) != 0;
+        float4* o4 = reinterpret_cast<float4*>(d.out_tiled ? out + (size_t)(line0 >> 1) * (2 * L)
+                                                           : out + (size_t)line0 * L);
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          const int e = t + T * s;
+          const float2 give = odd ? v0[s] : v1[s];
+          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, give.x, 1), __shfl_xor_sync(0xffffffffu, give.y, 1));
+          const float4 q = odd ? make_float4(got.x, got.y, v1[s].x, v1[s].y) : make_float4(v0[s].x, v0[s].y, got.x, got.y);
+          if (valid) o4[d.out_tiled ? e : (odd ? (L + e - 1) / 2 : e / 2)] = q;
+        }
+      } else if (valid) {
         if (d.out_tiled) {
           float2* o = out + (size_t)(line0 >> 1) * (2 * L);
 #pragma unroll
@@ -1230,9 +1285,6 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
   if (COL && tid == 0) bulk_wait_all();
 }
 
-#ifndef NSLCT_PAIR
-#define NSLCT_PAIR 1
-#endif
 
 template <typename R, int L, bool COL>
 inline int launch_one(const PassDesc& d, cudaStream_t s) {

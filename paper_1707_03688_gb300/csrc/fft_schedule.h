@@ -62,6 +62,16 @@ __host__ __device__ constexpr int stage_table_offset(int L, int E, int st) {
   for (int i = 1; i < st; ++i) off += stage_ns(L, E, i) * stage_radix(L, E, i);
   return off;
 }
-__host__ __device__ constexpr int twiddle_table_size(int L, int E) { return stage_table_offset(L, E, num_stages(L, E)); }
+// After the [jm][r] tables, a compact table per stage st >= 1 of the NS
+// base twiddles W_{NS*RD}^{jm} alone (the line-pair kernel forms the powers
+// r = 2 .. RD-1 in registers from these).
+__host__ __device__ constexpr int compact_table_offset(int L, int E, int st) {
+  int off = stage_table_offset(L, E, num_stages(L, E));
+  for (int i = 1; i < st; ++i) off += stage_ns(L, E, i);
+  return off;
+}
+__host__ __device__ constexpr int twiddle_table_size(int L, int E) {
+  return compact_table_offset(L, E, num_stages(L, E));
+}
 
 }  // namespace nslct
