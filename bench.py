@@ -403,11 +403,75 @@ def run_batch_workload(args, world, rank):
         "per_field_launches": {"ms_per_step": ms_each, "value": samples / (ms_each * 1e-3) / 1e6},
         "all_batched_no_graph": {"ms_per_step": ms_all_batched, "value": samples / (ms_all_batched * 1e-3) / 1e6},
         "tuned_no_graph": {"ms_per_step": ms_launch, "value": samples / (ms_launch * 1e-3) / 1e6},
-        "gpu_launches": 5 + 5 * sum(1 for nx, ny in shapes if max(nx, ny) >= split), "clocks": clk.summary(),
+        "gpu_launches": 5 + 5 * sum(1 for nx, ny in shapes if min(nx, ny) >= split), "clocks": clk.summary(),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
+
+
+def run_filter_workload(args, world, rank):
+    """Filtering in two NsLCT domains (Sec. 5.B) on the 4096^2 field: Eq. Add04
+    (two masked forwards, two inverses) and Eq. Add08 (two masked forwards,
+    one inverse of the composed matrix), each captured in one CUDA graph."""
+    import torch
+    from paper_1707_03688_gb300 import inputs as I
+    from paper_1707_03688_gb300 import nslct as N
+    N.load()
+    g, _ = _make_inputs()
+    m1, m3 = I.random_symplectic_abcd(300), I.random_symplectic_abcd(301)
+    q1, q3, q31 = N.Plan(m1, NX, NY), N.Plan(m3, NX, NY), N.Plan(m3 @ m1, NX, NY)
+    x = torch.from_numpy(g).to(torch.complex64).cuda()
+    h1 = torch.from_numpy(I.gaussian_mask(NX, NY, 0.3, tilt=2.0)).to(torch.complex64).cuda()
+    h3 = torch.from_numpy(I.gaussian_mask(NX, NY, 0.4)).to(torch.complex64).cuda()
+    y1, y2, y3, out04, out08 = (torch.empty_like(x) for _ in range(5))
+
+    def add04():
+        q1.forward(x, out=y1, mask=h1)
+        q3.forward(y1, out=y2, mask=h3)
+        q3.inverse(y2, out=y3)
+        q1.inverse(y3, out=out04)
+
+    def add08():
+        q1.forward(x, out=y1, mask=h1)
+        q3.forward(y1, out=y2, mask=h3)
+        q31.inverse(y2, out=out08)
+
+    stream = torch.cuda.Stream()
+    graphs = {}
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            add04()
+            add08()
+    torch.cuda.synchronize()
+    for name, fn in (("add04", add04), ("add08", add08)):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=stream):
+            fn()
+        graphs[name] = gr
+    res = {}
+    with torch.cuda.stream(stream), ClockSampler(torch.cuda.current_device()) as clk:
+        for name, gr in graphs.items():
+            res[name] = _timed(gr.replay, args.steps, args.warmup, stream)
+    torch.cuda.synchronize()
+    diff = float((torch.linalg.vector_norm(out08 - out04) / torch.linalg.vector_norm(out04)).item())
+    n = NX * NY
+    line = {
+        "metric": "NsLCT-domain filtering Msamples/s (Eq. Add08 pipeline)", "value": n / (res["add08"] * 1e-3) / 1e6,
+        "unit": "Msamples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["add08"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "4096x4096 complex64, Gaussian masks in the M1 and M3 domains (ABCD seeds 300, 301), "
+                               "each pipeline one CUDA graph",
+                   "transforms": {"add04": 4, "add08": 3}},
+        "add04": {"ms_per_step": res["add04"], "value": n / (res["add04"] * 1e-3) / 1e6},
+        "rel_l2_add08_vs_add04": diff,
+        "gpu_launches": 3 * 5, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for q in (q1, q3, q31):
+        q.close()
 
 
 def run_grad_workload(args, world, rank):
@@ -467,9 +531,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="fp32", choices=["fp32", "batch", "grad"],
+    ap.add_argument("--workload", default="fp32", choices=["fp32", "batch", "grad", "filter"],
                     help="fp32: 4096^2 x 16 ABCD (the benchmark line); batch: 256 uneven fields; "
-                         "grad: 64 x 1024^2 forward + backward")
+                         "grad: 64 x 1024^2 forward + backward; filter: two-domain filtering, Eqs. Add04/Add08")
     ap.add_argument("--method", default="ha", choices=["ha", "lc_y"],
                     help="H of Eq. HA24 (five passes) or of Eq. LC10 (three passes)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
@@ -486,6 +550,8 @@ def main():
         run_batch_workload(args, world, rank)
     elif args.workload == "grad":
         run_grad_workload(args, world, rank)
+    elif args.workload == "filter":
+        run_filter_workload(args, world, rank)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

@@ -73,6 +73,8 @@ typedef struct CUstream_st* nslct_stream_t;  /* same type as cudaStream_t */
  * (0,0;0,h) (Eq. LC10, or H = 0) run in three passes: CC^H then convolves
  * along y only and shares one row pass with CM^{C2} (see nslct_plan_passes). */
 #define NSLCT_FULL_CHAIN    0x20u
+/* nslct_plan_padded: return only the centred Nx x Ny region of the padded output. */
+#define NSLCT_CROP_OUTPUT   0x40u
 /* Arithmetic of the transform. */
 #define NSLCT_PREC_FP32     0x000u /* complex64 data, FP32 FFT arithmetic (default) */
 #define NSLCT_PREC_FP64     0x100u /* complex128 data, FP64 arithmetic throughout */
@@ -158,6 +160,41 @@ int nslct_forward(nslct_plan_t plan, const void* in, void* out, nslct_stream_t s
  * nslct_forward. Because L is unitary (Sec. 6.B), this is also L^H.
  */
 int nslct_inverse(nslct_plan_t plan, const void* in, void* out, nslct_stream_t stream);
+
+/*
+ * nslct_plan_padded -- zero padding (Sec. 2.A; Sec. 5.A pads the input to
+ * (N + dN) x (N + dN) against aliasing): the chain runs on the Nx_pad x Ny_pad
+ * grid (supported lengths, Nx_pad >= Nx, Ny_pad >= Ny), with the caller's
+ * Nx x Ny input (even sizes) at the centre: its row i is row
+ * i + Nx_pad/2 - Nx/2 of the grid, likewise for columns, and zeros elsewhere.
+ * The zeros are never stored: the first pass reads only the input's rows and
+ * the rest of each line is zero in shared memory. nslct_forward then reads an
+ * Nx x Ny array and writes the whole Nx_pad x Ny_pad output, or, with
+ * NSLCT_CROP_OUTPUT, only its centred Nx x Ny region (the last pass stores
+ * that region alone). nslct_inverse maps the output's shape back to the
+ * input's: it zero-pads its input the same way and returns the centred
+ * Nx x Ny region, so inverse(forward(x)) = x without cropping. dx, dy are the
+ * sample spacings of the input (kept on the padded grid); the frequency
+ * spacings become 2 pi / (N_pad dx). The plan owns an Nx_pad x Ny_pad work
+ * field. In-place calls are rejected (NSLCT_E_ARG); nslct_backward and
+ * batches do not take padded plans (NSLCT_E_UNSUPPORTED).
+ */
+int nslct_plan_padded(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, int Nx_pad, int Ny_pad,
+                      double dx, double dy, unsigned flags);
+
+/* nslct_plan_shape -- the caller-side shapes: input rows x cols and output
+ * rows x cols (both Nx x Ny for unpadded plans). Any pointer may be null. */
+int nslct_plan_shape(nslct_plan_t plan, int* in_rows, int* in_cols, int* out_rows, int* out_cols);
+
+/*
+ * nslct_forward_masked -- out = mask .* (L in): the forward transform followed
+ * by a pointwise filter in the NsLCT domain (the H1, H3 of Eqs. Add04/Add08),
+ * multiplied in the last pass before the store, so it costs one read of the
+ * mask instead of a separate pass. mask: device array of the output's shape
+ * and type (row-major, 16-byte aligned), not modified; it must not overlap
+ * `out`. Same errors as nslct_forward, NSLCT_E_ARG for a null or misaligned mask.
+ */
+int nslct_forward_masked(nslct_plan_t plan, const void* in, const void* mask, void* out, nslct_stream_t stream);
 
 /*
  * nslct_plan_passes -- kernel passes per transform of this plan: 5, or 3 for
@@ -288,7 +325,7 @@ int nslct_batch_forward(nslct_batch_t batch, nslct_stream_t stream);
 int nslct_batch_capture(nslct_batch_t batch, nslct_stream_t stream);
 
 /*
- * nslct_batch_set_split -- fields whose longer side is >= `split` run through
+ * nslct_batch_set_split -- fields whose shorter side is >= `split` run through
  * their own plan's fused passes (as nslct_forward), enqueued before the batched
  * launches; the others stay in the batched launches. The default (2^30)
  * batches every field. Drops a captured graph. nslct_batch_get_split returns it.
@@ -298,7 +335,7 @@ int nslct_batch_get_split(nslct_batch_t batch);
 
 /*
  * nslct_batch_tune -- autotune the split on the bound buffers: for every
- * distinct field size (and "batch everything") run one warm-up forward and
+ * distinct shorter side (and "batch everything") run one warm-up forward and
  * `iters` timed forwards on `stream` (CUDA events), keep the fastest, and
  * return it in *chosen (nullable) with its time per forward in
  * *ms_per_forward (nullable). Synchronises `stream`. Overwrites the bound

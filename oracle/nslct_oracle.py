@@ -439,6 +439,67 @@ def inverse(big_g, params, dx: float, dy: float) -> np.ndarray:
     return x
 
 
+def zero_pad(g, nx_pad: int, ny_pad: int) -> np.ndarray:
+    """Zero-pad an Nx x Ny field to Nx_pad x Ny_pad (Sec. 2.A; Sec. 5.A pads
+    the input to (N + dN) x (N + dN) against aliasing) keeping each sample at
+    its centred index: row i of the field (index i - floor(Nx/2)) becomes row
+    i + floor(Nx_pad/2) - floor(Nx/2) of the padded grid."""
+    g = np.asarray(g, dtype=np.complex128)
+    nx, ny = g.shape
+    out = np.zeros((nx_pad, ny_pad), dtype=np.complex128)
+    r0, c0 = nx_pad // 2 - nx // 2, ny_pad // 2 - ny // 2
+    out[r0:r0 + nx, c0:c0 + ny] = g
+    return out
+
+
+def centre_crop(x, nx: int, ny: int) -> np.ndarray:
+    """The Nx x Ny region of a larger grid at the same centred indices (the
+    inverse of zero_pad on its support)."""
+    x = np.asarray(x)
+    r0, c0 = x.shape[0] // 2 - nx // 2, x.shape[1] // 2 - ny // 2
+    return x[r0:r0 + nx, c0:c0 + ny]
+
+
+def forward_padded(g, params, dx: float, dy: float, nx_pad: int, ny_pad: int, crop: bool = False):
+    """The chain of Eq. HA28 on the zero-padded input, with the same sample
+    spacing (so the frequency spacing becomes 2 pi / (N_pad dx)); the whole
+    padded output, or its centred input-sized region."""
+    out = forward(zero_pad(g, nx_pad, ny_pad), params, dx, dy)
+    return centre_crop(out, *np.shape(g)) if crop else out
+
+
+def inverse_padded(big_g, params, dx: float, dy: float, nx_pad: int, ny_pad: int, nx: int, ny: int):
+    """Inverse chain on the padded grid: the input (the padded output, or its
+    centred crop) is zero-padded to the grid, and the centred Nx x Ny region
+    of the result is returned."""
+    return centre_crop(inverse(zero_pad(big_g, nx_pad, ny_pad), params, dx, dy), nx, ny)
+
+
+def filter_two_domains(g, params1, params3, h1, h3, dx: float, dy: float):
+    """Eq. Add04: filter h1 in the NsLCT domain of M1, then h3 in that of M3,
+    and back to space through both inverses (each the exact inverse chain of
+    its plan, Eq. CCCMCCCM04). The (A3,B3;C3,D2) printed inside Eq. Add04 is
+    read as M3."""
+    y = np.asarray(h1) * forward(g, params1, dx, dy)
+    y = np.asarray(h3) * forward(y, params3, dx, dy)
+    return inverse(inverse(y, params3, dx, dy), params1, dx, dy)
+
+
+def filter_two_domains_additive(g, params1, params3, params31, h1, h3, dx: float, dy: float):
+    """Eq. Add08: the same two filters, but one inverse transform of the
+    composed matrix M3 M1 (params31) replaces the two inverses; exact only
+    if the NsDLCT were additive."""
+    y = np.asarray(h1) * forward(g, params1, dx, dy)
+    y = np.asarray(h3) * forward(y, params3, dx, dy)
+    return inverse(y, params31, dx, dy)
+
+
+def nmse_add(g, params1, params3, params31, dx: float, dy: float) -> float:
+    """Eq. Add16 with G = L_{M3}(L_{M1} g) (Eq. Add20) and G' = L_{M3 M1} g (Eq. Add22)."""
+    big = forward(forward(g, params1, dx, dy), params3, dx, dy)
+    return nmse(forward(g, params31, dx, dy), big)
+
+
 def transform(g, m, dx: float, dy: float, h=None, method: str = "ha"):
     """Plan and apply the NsDLCT for ABCD ``m``."""
     return forward(g, plan(m, h=h, method=method), dx, dy)

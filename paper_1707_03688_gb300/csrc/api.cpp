@@ -67,6 +67,7 @@ int upload_twiddles(int L, int E, void** dev) {
 void free_plan(nslct_plan_s* p) {
   if (!p) return;
   if (p->ws) cudaFree(p->ws);
+  if (p->pad_ws) cudaFree(p->pad_ws);
   if (p->err) cudaFree(p->err);
   if (p->partials) cudaFree(p->partials);
   // the four twiddle pointers may alias each other: free each table once
@@ -85,10 +86,12 @@ int launch(const nslct_plan_s* p, bool col, const PassDesc& d, cudaStream_t s) {
 
 // Enqueue passes [first, last] of the forward (or inverse) chain.
 int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, bool inverse, int first = 0,
-              int last = 4) {
+              int last = 4, const void* mask = nullptr) {
   if (!p || !in || !out || first < 0 || last > 4 || first > last) return NSLCT_E_ARG;
   // 16-byte copies need 16-byte aligned fields
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return NSLCT_E_ARG;
+  // a padded plan's input and output have different shapes: no in-place calls
+  if (p->padded && in == out) return NSLCT_E_ARG;
   DeviceGuard g(p->device);
   if (!g.ok) return NSLCT_E_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -96,6 +99,10 @@ int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, 
   bool cols[5];
   const int npass = build_schedule(p, in, out, inverse, d, cols);
   if (last >= npass) return NSLCT_E_ARG;
+  if (mask) {
+    if (reinterpret_cast<uintptr_t>(mask) & 15u) return NSLCT_E_ARG;
+    d[npass - 1].post_mask = mask;
+  }
   for (int k = first; k <= last; ++k) {
     const int rc = launch(p, cols[k], d[k], s);
     if (rc != NSLCT_OK) return rc;
@@ -112,6 +119,28 @@ bool chain_pass_is_column(int k) { return k == 1 || k == 3; }
 // The five passes of the forward chain (Eq. HA28, right to left) or of the
 // inverse chain (Eq. CCCMCCCM04) from `in` (row-major) to `out` (row-major),
 // with `out` holding the tiled intermediate field between passes.
+// The tiled grid between passes: the caller's output buffer, unless the
+// caller's output is smaller than the grid (padded plans).
+void* chain_mid(const nslct_plan_s* p, void* out, bool inverse) {
+  if (!p->padded) return out;
+  const bool small_out = inverse ? (p->in_rows != p->Nx || p->in_cols != p->Ny)
+                                 : (p->out_rows != p->Nx || p->out_cols != p->Ny);
+  return small_out ? p->pad_ws : out;
+}
+
+// Set the zero-padding regions of a chain's first (row-major input) and last
+// (row-major output) pass: the forward reads the input region and writes the
+// output region, the inverse the other way round.
+void set_pad_regions(const nslct_plan_s* p, bool inverse, PassDesc& first, PassDesc& last) {
+  if (!p->padded) return;
+  const int* src = inverse ? &p->out_rows : &p->in_rows;
+  const int* dst = inverse ? &p->in_rows : &p->out_rows;
+  first.pad_in = (src[0] != p->Nx || src[1] != p->Ny) ? 1 : 0;
+  first.in_rows = src[0]; first.in_cols = src[1]; first.in_r0 = src[2]; first.in_c0 = src[3];
+  last.pad_out = (dst[0] != p->Nx || dst[1] != p->Ny) ? 1 : 0;
+  last.out_rows = dst[0]; last.out_cols = dst[1]; last.out_r0 = dst[2]; last.out_c0 = dst[3];
+}
+
 void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool inverse, PassDesc d[5]) {
   const double ccs = -1.0 / ((double)p->Nx * (double)p->Ny);  // each CC's constant, Eq. BasicDFT16/20
   PassDesc base{};
@@ -120,11 +149,14 @@ void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool in
   base.scale = 1.0;
   base.fscale2 = 1.0f;
   for (int k = 0; k < 5; ++k) d[k] = base;
-  // pass 1: row pass, caller layout -> tiled layout in `out`
-  d[0].in = in; d[0].out = out; d[0].in_tiled = 0; d[0].out_tiled = 1; d[0].tw = p->tw_y;
-  // passes 2..4 in place on the tiled field; pass 5 back to the caller layout
-  for (int k = 1; k < 5; ++k) { d[k].in = out; d[k].out = out; d[k].in_tiled = 1; d[k].out_tiled = 1; }
+  void* mid = chain_mid(p, out, inverse);
+  // pass 1: row pass, caller layout -> tiled layout in `mid`
+  d[0].in = in; d[0].out = mid; d[0].in_tiled = 0; d[0].out_tiled = 1; d[0].tw = p->tw_y;
+  // passes 2..4 in place on the tiled field; pass 5 back to the caller layout in `out`
+  for (int k = 1; k < 5; ++k) { d[k].in = mid; d[k].out = mid; d[k].in_tiled = 1; d[k].out_tiled = 1; }
+  d[4].out = out;
   d[4].out_tiled = 0;
+  set_pad_regions(p, inverse, d[0], d[4]);
   d[1].tw = p->tw_x; d[2].tw = p->tw_y; d[3].tw = p->tw_x; d[4].tw = p->tw_y;
   d[1].freq_domain = d[3].freq_domain = 1;
   d[1].has_chirp = d[2].has_chirp = d[3].has_chirp = 1;
@@ -198,9 +230,14 @@ int build_schedule(const nslct_plan_s* p, const void* in, void* out, bool invers
   }
   // r1 reads the caller's field and writes the tiled one; c2 works in place;
   // r3 returns to the caller's layout in `out`
-  r1.in = in; r1.out = out; r1.in_tiled = 0; r1.out_tiled = 1;
-  c2.in = out; c2.out = out; c2.in_tiled = 1; c2.out_tiled = 1;
-  r3.in = out; r3.out = out; r3.in_tiled = 1; r3.out_tiled = 0;
+  void* mid = chain_mid(p, out, inverse);
+  r1.in = in; r1.out = mid; r1.in_tiled = 0; r1.out_tiled = 1;
+  c2.in = mid; c2.out = mid; c2.in_tiled = 1; c2.out_tiled = 1;
+  r3.in = mid; r3.out = out; r3.in_tiled = 1; r3.out_tiled = 0;
+  c2.pad_in = c2.pad_out = 0;
+  r1.pad_out = 0;
+  r3.pad_in = 0;
+  set_pad_regions(p, inverse, r1, r3);
   d[0] = r1; d[1] = c2; d[2] = r3;
   cols[0] = false; cols[1] = true; cols[2] = false;
   return 3;
@@ -373,6 +410,47 @@ int nslct_plan_theta_get(nslct_plan_t p, double theta[10]) {
   return NSLCT_OK;
 }
 
+int nslct_plan_padded(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, int Nx_pad, int Ny_pad, double dx,
+                      double dy, unsigned flags) {
+  if (!out) return NSLCT_E_ARG;
+  *out = nullptr;
+  if ((flags & NSLCT_H_MASK) == NSLCT_H_USER) return NSLCT_E_ARG;
+  if (Nx < 2 || Ny < 2 || (Nx & 1) || (Ny & 1) || Nx > Nx_pad || Ny > Ny_pad) return NSLCT_E_ARG;
+  const bool crop = (flags & NSLCT_CROP_OUTPUT) != 0;
+  int rc = nslct_plan_ex(out, abcd, Nx_pad, Ny_pad, dx, dy, flags & ~NSLCT_CROP_OUTPUT, nullptr);
+  if (rc != NSLCT_OK) return rc;
+  nslct_plan_s* p = *out;
+  p->flags = flags;
+  p->padded = 1;
+  // centred placement: index i of the field sits at i - floor(N/2) of the
+  // centred grid, i.e. at row i + floor(N'/2) - floor(N/2)
+  p->in_rows = Nx; p->in_cols = Ny;
+  p->in_r0 = Nx_pad / 2 - Nx / 2; p->in_c0 = Ny_pad / 2 - Ny / 2;
+  if (crop) {
+    p->out_rows = Nx; p->out_cols = Ny; p->out_r0 = p->in_r0; p->out_c0 = p->in_c0;
+  } else {
+    p->out_rows = Nx_pad; p->out_cols = Ny_pad; p->out_r0 = 0; p->out_c0 = 0;
+  }
+  const size_t esz = p->prec == 1 ? 16 : 8;
+  DeviceGuard g(p->device);
+  if (!g.ok || cudaMalloc(&p->pad_ws, esz * (size_t)Nx_pad * Ny_pad) != cudaSuccess) {
+    p->pad_ws = nullptr;
+    free_plan(p);
+    *out = nullptr;
+    return NSLCT_E_NOMEM;
+  }
+  return NSLCT_OK;
+}
+
+int nslct_plan_shape(nslct_plan_t p, int* in_rows, int* in_cols, int* out_rows, int* out_cols) {
+  if (!p) return NSLCT_E_ARG;
+  if (in_rows) *in_rows = p->padded ? p->in_rows : p->Nx;
+  if (in_cols) *in_cols = p->padded ? p->in_cols : p->Ny;
+  if (out_rows) *out_rows = p->padded ? p->out_rows : p->Nx;
+  if (out_cols) *out_cols = p->padded ? p->out_cols : p->Ny;
+  return NSLCT_OK;
+}
+
 int nslct_plan(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, double dx, double dy, unsigned flags) {
   if ((flags & NSLCT_H_MASK) == NSLCT_H_USER) return NSLCT_E_ARG;
   return nslct_plan_ex(out, abcd, Nx, Ny, dx, dy, flags, nullptr);
@@ -405,6 +483,11 @@ int nslct_inverse(nslct_plan_t p, const void* in, void* out, nslct_stream_t stre
 }
 
 int nslct_plan_passes(nslct_plan_t p) { return !p ? 0 : (p->y_only_h ? 3 : 5); }
+
+int nslct_forward_masked(nslct_plan_t p, const void* in, const void* mask, void* out, nslct_stream_t stream) {
+  if (!mask) return NSLCT_E_ARG;
+  return run_chain(p, in, out, stream, false, 0, p ? nslct_plan_passes(p) - 1 : 4, mask);
+}
 
 int nslct_forward_pass(nslct_plan_t p, int pass, const void* in, void* out, nslct_stream_t stream) {
   if (!p || pass < 0 || pass >= nslct_plan_passes(p)) return NSLCT_E_ARG;

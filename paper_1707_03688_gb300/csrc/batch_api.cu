@@ -19,7 +19,7 @@ struct nslct_batch_s {
   int item_off[5] = {0};
   int nitems[5] = {0};
   int* d_counters = nullptr;        // one per pass
-  // fields whose longer side is >= split run through their own plan's fused
+  // fields whose shorter side is >= split run through their own plan's fused
   // kernels (nslct_forward) instead of the batched launches; chosen by
   // nslct_batch_tune (default: every field batched)
   int split = 1 << 30;
@@ -45,7 +45,7 @@ void free_batch(nslct_batch_s* b) {
   delete b;
 }
 
-bool runs_alone(const nslct_batch_s* b, int f) { return std::max(b->Nx[f], b->Ny[f]) >= b->split; }
+bool runs_alone(const nslct_batch_s* b, int f) { return std::min(b->Nx[f], b->Ny[f]) >= b->split; }
 
 // (Re)build the per-pass work lists of the batched fields: every field's
 // panels, longest lines first.
@@ -196,9 +196,9 @@ int nslct_batch_tune(nslct_batch_t b, nslct_stream_t stream, int iters, int* cho
     if (b->in[f] == b->out[f]) return NSLCT_E_ARG;  // the timing runs must not feed outputs back in
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   drop_graph(b);
-  // candidate thresholds: the distinct field sizes (largest side), and "none"
+  // candidate thresholds: the distinct shorter sides, and "none"
   std::vector<int> cands;
-  for (int f = 0; f < b->n; ++f) cands.push_back(std::max(b->Nx[f], b->Ny[f]));
+  for (int f = 0; f < b->n; ++f) cands.push_back(std::min(b->Nx[f], b->Ny[f]));
   std::sort(cands.begin(), cands.end());
   cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
   cands.push_back(1 << 30);

@@ -202,12 +202,33 @@ template <typename R> struct Dft<R, 64> : DftComposite<R, 8, 8> {};
 __device__ __forceinline__ int padded(int e) { return e + (e >> 4); }
 template <int SH> __device__ __forceinline__ int padded_by(int e) { return e + (e >> SH); }
 
-// Twiddles of stage ST for butterfly jm: tab[OFF + jm*RD + r] = W_{NS*RD}^{jm*r}.
+// LM (line-major): the T_LINE threads of line p are threads p*T_LINE .. ,
+// whole warps, so each line keeps its exchange buffer to itself
+// (p*(L + L/16) + padded(e)) and synchronises on its own named barrier
+// (1 + p) instead of the whole CTA. Otherwise lines are interleaved thread by
+// thread (padded(e)*P + p) and share __syncthreads.
+// w[r] = w1^r for r = 1 .. RD-1 (w[0] unused), each as w[2^k] * w[r - 2^k] with
+// w[2^k] by repeated squaring: at most four roundings deep for RD = 16. This
+// replaces RD-1 table loads per butterfly by one load of the base twiddle
+// W_{NS*RD}^{jm} (the compact table) and RD-2 complex products.
+template <typename R, int RD>
+__device__ __forceinline__ void twiddle_powers(cpx<R> w1, cpx<R>* w) {
+  w[1] = w1;
+#pragma unroll
+  for (int r = 2; r < RD; ++r) {
+    const int hi = (r & (r - 1)) == 0 ? r / 2 : (1 << (31 - __clz(r)));
+    const int lo = (r & (r - 1)) == 0 ? r / 2 : r - hi;
+    w[r] = cmul<R>(w[hi], w[lo]);
+  }
+}
+
+// Twiddles of stage ST for butterfly jm from the full table,
+// tab[OFF + jm*RD + r] = W_{NS*RD}^{jm*r}: each correctly rounded (used where
+// the extra rounding of the register powers matters, the adjoint kernels).
 template <typename R, int RD>
 __device__ __forceinline__ void load_twiddles(const cpx<R>* __restrict__ row, cpx<R>* w) {
   if constexpr (sizeof(R) == 4 && RD % 2 == 0) {
-    // two complex64 per 16-byte load; rows start at even entries
-    const float4* p4 = reinterpret_cast<const float4*>(row);
+    const float4* p4 = reinterpret_cast<const float4*>(row);  // rows start at even entries
 #pragma unroll
     for (int r = 0; r < RD; r += 2) {
       const float4 q = __ldg(p4 + r / 2);
@@ -220,12 +241,9 @@ __device__ __forceinline__ void load_twiddles(const cpx<R>* __restrict__ row, cp
   }
 }
 
-// LM (line-major): the T_LINE threads of line p are threads p*T_LINE .. ,
-// whole warps, so each line keeps its exchange buffer to itself
-// (p*(L + L/16) + padded(e)) and synchronises on its own named barrier
-// (1 + p) instead of the whole CTA. Otherwise lines are interleaved thread by
-// thread (padded(e)*P + p) and share __syncthreads.
-template <typename R, int L, int P, int E_ = elems_per_thread(L), bool LM = false>
+// EXACT = true: table twiddles (load_twiddles); false: one base twiddle per
+// butterfly and its powers in registers (twiddle_powers).
+template <typename R, int L, int P, int E_ = elems_per_thread(L), bool LM = false, bool EXACT = false>
 struct LineFft {
   static constexpr int E = E_;
   static constexpr int T_LINE = L / E;
@@ -272,7 +290,8 @@ struct LineFft {
       const int jm = j % NS;
       if constexpr (NS > 1) {
         cpx<R> w[RD];
-        load_twiddles<R, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+        if constexpr (EXACT) load_twiddles<R, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+        else twiddle_powers<R, RD>(tw[compact_table_offset(L, E, ST) + jm], w);
 #pragma unroll
         for (int r = 1; r < RD; ++r) x[r] = cmul<R>(x[r], w[r]);
       }
@@ -487,7 +506,7 @@ struct MixedLineFft {
       const int jm = j % NS;
       if constexpr (NS > 1) {
         float2 w[RD];
-        load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+        twiddle_powers<float, RD>(__ldg(tw + compact_table_offset(L, E, ST) + jm), w);
 #pragma unroll
         for (int r = 1; r < RD; ++r) x[r] = cmul<float>(x[r], w[r]);
       }
@@ -548,6 +567,18 @@ __device__ __forceinline__ double2 chirp_value(uint64_t q, double scale) {
 }
 
 __device__ __forceinline__ int centred_bin(int b, int n) { return b < (n + 1) / 2 ? b : b - n; }
+
+// Output-domain mask of a row-major output pass: value (i, j) of the grid is
+// multiplied by the mask element at the same output position (the output
+// region's coordinates for a cropped padded plan); positions outside the
+// stored region are left alone.
+template <typename R>
+__device__ __forceinline__ cpx<R> apply_post_mask(const PassDesc& d, int i, int j, cpx<R> v) {
+  const int rows = d.pad_out ? d.out_rows : d.Nx, cols = d.pad_out ? d.out_cols : d.Ny;
+  const int r = d.pad_out ? i - d.out_r0 : i, c = d.pad_out ? j - d.out_c0 : j;
+  if ((unsigned)r >= (unsigned)rows || (unsigned)c >= (unsigned)cols) return v;
+  return cmul<R>(v, reinterpret_cast<const cpx<R>*>(d.post_mask)[(size_t)r * cols + c]);
+}
 
 // element (i, j) of an Nx x Ny field in the given layout
 __device__ __forceinline__ int elem_index(int i, int j, int Ny, int tiled) {
@@ -647,7 +678,15 @@ pass_kernel(PassDesc d) {
     const int e = t + T_LINE * s;
     const int i = COL ? e : line;
     const int j = COL ? line : e;
-    v[s] = valid ? in[elem_index(i, j, d.Ny, d.in_tiled)] : mk<R>((R)0, (R)0);
+    if (!COL && !d.in_tiled && d.pad_in) {
+      // zero padding: the caller's array is the region at (in_r0, in_c0)
+      const int r = i - d.in_r0, c = j - d.in_c0;
+      v[s] = (valid && (unsigned)r < (unsigned)d.in_rows && (unsigned)c < (unsigned)d.in_cols)
+                 ? in[(size_t)r * d.in_cols + c]
+                 : mk<R>((R)0, (R)0);
+    } else {
+      v[s] = valid ? in[elem_index(i, j, d.Ny, d.in_tiled)] : mk<R>((R)0, (R)0);
+    }
   }
 
   if (d.t1 != kNone) LineFft<R, L, P>::run(v, sm, t, p, tw, d.t1 == kInv);
@@ -659,6 +698,10 @@ pass_kernel(PassDesc d) {
     for (int s = 0; s < E; ++s) v[s] = mk<R>(v[s].x * scale, v[s].y * scale);
   }
   if (d.t2 != kNone) LineFft<R, L, P>::run(v, sm, t, p, tw, d.t2 == kInv);
+  if (!COL && !d.out_tiled && d.post_mask && valid) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = apply_post_mask<R>(d, line, t + T_LINE * s, v[s]);
+  }
 
   // In-place passes: every thread of the CTA must have loaded its inputs before
   // any thread stores (the FFT stages already synchronise when S > 1).
@@ -670,7 +713,12 @@ pass_kernel(PassDesc d) {
       const int e = t + T_LINE * s;
       const int i = COL ? e : line;
       const int j = COL ? line : e;
-      out[elem_index(i, j, d.Ny, d.out_tiled)] = v[s];
+      if (!COL && !d.out_tiled && d.pad_out) {
+        const int r = i - d.out_r0, c = j - d.out_c0;
+        if ((unsigned)r < (unsigned)d.out_rows && (unsigned)c < (unsigned)d.out_cols) out[(size_t)r * d.out_cols + c] = v[s];
+      } else {
+        out[elem_index(i, j, d.Ny, d.out_tiled)] = v[s];
+      }
     }
   }
 }
@@ -803,9 +851,21 @@ __device__ __forceinline__ void tma_load_panel(float2* stg, const float2* in, co
       mbar_arrive_expect_tx(bar, (uint32_t)((valid >> 1) * 2 * L * sizeof(float2)));
       for (int q = 0; q < (valid >> 1); ++q)
         bulk_load(stg + q * (2 * L), in + (size_t)((first >> 1) + q) * (2 * L), 2 * L * sizeof(float2), bar);
-    } else {
+    } else if (!d.pad_in) {
       mbar_arrive_expect_tx(bar, (uint32_t)(valid * L * sizeof(float2)));
       for (int q = 0; q < valid; ++q) bulk_load(stg + q * (L + 8), in + (size_t)(first + q) * L, L * sizeof(float2), bar);
+    } else {
+      // zero padding: only the caller's rows, copied to the 16-byte boundary
+      // at or below the column offset (read back shifted)
+      uint32_t bytes = 0;
+      for (int q = 0; q < valid; ++q)
+        if ((unsigned)(first + q - d.in_r0) < (unsigned)d.in_rows) bytes += d.in_cols * sizeof(float2);
+      mbar_arrive_expect_tx(bar, bytes);
+      for (int q = 0; q < valid; ++q) {
+        const int r = first + q - d.in_r0;
+        if ((unsigned)r < (unsigned)d.in_rows)
+          bulk_load(stg + q * (L + 8) + (d.in_c0 & ~1), in + (size_t)r * d.in_cols, d.in_cols * sizeof(float2), bar);
+      }
     }
   }
 }
@@ -890,8 +950,18 @@ pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __
       return;
     }
     float2 v[E];
+    if (COL || d.in_tiled || !d.pad_in) {
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = buf[stg_index<L, COL, P>(p, t + T_LINE * s, d.in_tiled)];
+      for (int s = 0; s < E; ++s) v[s] = buf[stg_index<L, COL, P>(p, t + T_LINE * s, d.in_tiled)];
+    } else {
+      const bool rv = (unsigned)(line - d.in_r0) < (unsigned)d.in_rows;
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const int e = t + T_LINE * s;
+        v[s] = (rv && (unsigned)(e - d.in_c0) < (unsigned)d.in_cols) ? buf[p * (L + 8) + e - (d.in_c0 & 1)]
+                                                                       : make_float2(0.f, 0.f);
+      }
+    }
     __syncthreads();  // this input buffer is consumed
     const int next = panel + NIN * gridDim.x;
     if (tid == 0 && next < npanels) {
@@ -914,6 +984,10 @@ pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __
       for (int s = 0; s < E; ++s) v[s] = make_float2(v[s].x * d.fscale2, v[s].y * d.fscale2);
     }
     if (d.t3 != kNone) Fft::run(v, xs, t, p, tw, d.t3 == kInv);
+    if (!COL && !d.out_tiled && d.post_mask) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = apply_post_mask<float>(d, line, t + T_LINE * s, v[s]);
+    }
 
     if constexpr (COL) {
 #pragma unroll
@@ -921,6 +995,15 @@ pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __
       fence_proxy_async();
       __syncthreads();
       if (tid == 0) tma_store_panel<L, COL, P>(stg_out, out, &map_out, d, panel);
+    } else if (!d.out_tiled && d.pad_out) {
+      const int r = line - d.out_r0;
+      if ((unsigned)r < (unsigned)d.out_rows) {
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          const int c = t + T_LINE * s - d.out_c0;
+          if ((unsigned)c < (unsigned)d.out_cols) out[(size_t)r * d.out_cols + c] = v[s];
+        }
+      }
     } else if (valid) {
 #pragma unroll
       for (int s = 0; s < E; ++s) out[elem_index(line, t + T_LINE * s, d.Ny, d.out_tiled)] = v[s];
@@ -976,16 +1059,6 @@ template <int L> struct PairShape {
 
 // w[r] = w1^r for r = 1 .. RD-1 (w[0] unused), each as w[2^k] * w[r - 2^k] with
 // w[2^k] by repeated squaring: at most four roundings deep for RD = 16.
-template <int RD>
-__device__ __forceinline__ void twiddle_powers(float2 w1, float2* w) {
-  w[1] = w1;
-#pragma unroll
-  for (int r = 2; r < RD; ++r) {
-    const int hi = (r & (r - 1)) == 0 ? r / 2 : (1 << (31 - __clz(r)));
-    const int lo = (r & (r - 1)) == 0 ? r / 2 : r - hi;
-    w[r] = cmul<float>(w[hi], w[lo]);
-  }
-}
 
 template <int L> struct PairFft {
   using Sh = PairShape<L>;
@@ -1028,7 +1101,7 @@ template <int L> struct PairFft {
       if constexpr (NS > 1) {
         // one coalesced load of the base twiddle; its powers in registers
         float2 w[RD];
-        twiddle_powers<RD>(__ldg(tw + compact_table_offset(L, E, ST) + jm), w);
+        twiddle_powers<float, RD>(__ldg(tw + compact_table_offset(L, E, ST) + jm), w);
 #pragma unroll
         for (int r = 1; r < RD; ++r) {
           x0[r] = cmul<float>(x0[r], w[r]);
@@ -1103,12 +1176,27 @@ __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, con
     mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)));
     for (int g = 0; g < pairs; ++g)
       bulk_load(x + g * Sh::LS, in + (size_t)((first >> 1) + g) * (2 * L), 2 * L * sizeof(float2), bar);
-  } else {
+  } else if (!d.pad_in) {
     mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)));
     for (int g = 0; g < pairs; ++g)
       for (int h = 0; h < 2; ++h)
         bulk_load(reinterpret_cast<float2*>(x + g * Sh::LS) + h * (L + 8), in + (size_t)(first + 2 * g + h) * L,
                   L * sizeof(float2), bar);
+  } else {
+    // zero padding: only the caller's rows, each copied to the 16-byte
+    // boundary at or below its column offset (read back shifted)
+    uint32_t bytes = 0;
+    for (int g = 0; g < pairs; ++g)
+      for (int h = 0; h < 2; ++h)
+        if ((unsigned)(first + 2 * g + h - d.in_r0) < (unsigned)d.in_rows) bytes += d.in_cols * sizeof(float2);
+    mbar_arrive_expect_tx(bar, bytes);
+    for (int g = 0; g < pairs; ++g)
+      for (int h = 0; h < 2; ++h) {
+        const int r = first + 2 * g + h - d.in_r0;
+        if ((unsigned)r < (unsigned)d.in_rows)
+          bulk_load(reinterpret_cast<float2*>(x + g * Sh::LS) + h * (L + 8) + (d.in_c0 & ~1),
+                    in + (size_t)r * d.in_cols, d.in_cols * sizeof(float2), bar);
+      }
   }
 }
 
@@ -1187,11 +1275,22 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
           v1[s] = xg2[(e >> 1) * 4 + 2 + (e & 1)];
         }
       }
-    } else {
+    } else if (!d.pad_in) {
 #pragma unroll
       for (int s = 0; s < E; ++s) {
         v0[s] = xg2[t + T * s];
         v1[s] = xg2[(L + 8) + t + T * s];
+      }
+    } else {
+      const bool r0 = (unsigned)(line0 - d.in_r0) < (unsigned)d.in_rows;
+      const bool r1 = (unsigned)(line0 + 1 - d.in_r0) < (unsigned)d.in_rows;
+      const int shift = d.in_c0 & 1;
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const int e = t + T * s;
+        const bool c = (unsigned)(e - d.in_c0) < (unsigned)d.in_cols;
+        v0[s] = (c && r0) ? xg2[e - shift] : make_float2(0.f, 0.f);
+        v1[s] = (c && r1) ? xg2[(L + 8) + e - shift] : make_float2(0.f, 0.f);
       }
     }
 
@@ -1219,6 +1318,13 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       }
     }
     if (d.t3 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t3 == kInv);
+    if (!COL && !d.out_tiled && d.post_mask) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        v0[s] = apply_post_mask<float>(d, line0, t + T * s, v0[s]);
+        v1[s] = apply_post_mask<float>(d, line0 + 1, t + T * s, v1[s]);
+      }
+    }
     __syncthreads();  // every thread has finished reading the buffer
     const int next = panel + gridDim.x;
 
@@ -1245,7 +1351,18 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         fence_proxy_async();
         pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
       }
-      if constexpr (NSLCT_PAIR_SHFL) {
+      if (!d.out_tiled && d.pad_out) {
+        // zero padding: store the output region alone
+        const int r = line0 - d.out_r0;
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          const int c = t + T * s - d.out_c0;
+          if ((unsigned)c < (unsigned)d.out_cols) {
+            if ((unsigned)r < (unsigned)d.out_rows) out[(size_t)r * d.out_cols + c] = v0[s];
+            if ((unsigned)(r + 1) < (unsigned)d.out_rows) out[(size_t)(r + 1) * d.out_cols + c] = v1[s];
+          }
+        }
+      } else if constexpr (NSLCT_PAIR_SHFL) {
         // lanes e (even) and e^1 swap halves so that each lane stores one
         // 16-byte vector: tiled, float4 e; row-major, (line0[e], line0[e+1])
         // from the even lane and (line1[e-1], line1[e]) from the odd one
@@ -1417,8 +1534,8 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
     vy[s] = valid ? yin[k] : mk<R>((R)0, (R)0);
   }
   if (d.t1 != kNone) {
-    LineFft<R, L, P, E>::run(vg, sm, t, p, tw, d.t1 == kInv);
-    LineFft<R, L, P, E>::run(vy, sm, t, p, tw, d.t1 == kInv);
+    LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t1 == kInv);
+    LineFft<R, L, P, E, false, true>::run(vy, sm, t, p, tw, d.t1 == kInv);
   }
   if (accumulate) {
     // coordinates as in apply_chirp
@@ -1477,8 +1594,8 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
     }
   }
   if (d.t2 != kNone) {
-    LineFft<R, L, P, E>::run(vg, sm, t, p, tw, d.t2 == kInv);
-    LineFft<R, L, P, E>::run(vy, sm, t, p, tw, d.t2 == kInv);
+    LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t2 == kInv);
+    LineFft<R, L, P, E, false, true>::run(vy, sm, t, p, tw, d.t2 == kInv);
   }
   __syncthreads();  // in-place: all loads of the panel happened before any store
   if (valid) {

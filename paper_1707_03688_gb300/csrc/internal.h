@@ -51,6 +51,16 @@ struct PassDesc {
   int freq_domain2;
   Chirp chirp2;
   float fscale2;       // applied with chirp2 (or alone when != 1)
+  // zero padding (Secs. 2.A, 5.A): a pass with row-major input and pad_in set
+  // reads the caller's in_rows x in_cols array as the region starting at
+  // (in_r0, in_c0) of the Nx x Ny grid, zeros elsewhere; a pass with row-major
+  // output and pad_out set writes only the region at (out_r0, out_c0) to an
+  // out_rows x out_cols array
+  int pad_in, in_rows, in_cols, in_r0, in_c0;
+  int pad_out, out_rows, out_cols, out_r0, out_c0;
+  // a row-major output pass multiplies each stored value by the same element
+  // of this caller array (the output's shape and type) when non-null
+  const void* post_mask;
 };
 
 // Enqueue one pass. `col` selects the axis. Returns an NSLCT_* code.
@@ -112,4 +122,12 @@ struct nslct_plan_s {
   void* tw_y;          // device twiddles for length Ny (tables may alias each other)
   void* tw16_x;        // twiddles for elems_per_thread(Nx): adjoint and batched kernels
   void* tw16_y;
+  // zero padding: the caller's input field is the in_rows x in_cols region at
+  // (in_r0, in_c0) of the Nx x Ny grid the chain runs on; the output is the
+  // out_* region (the whole grid unless cropped). pad_ws holds the tiled grid
+  // between passes when the caller's output is smaller than the grid.
+  int padded;
+  int in_rows, in_cols, in_r0, in_c0;
+  int out_rows, out_cols, out_r0, out_c0;
+  void* pad_ws;
 };

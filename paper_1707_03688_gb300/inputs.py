@@ -26,6 +26,7 @@ import numpy as np
 __all__ = [
     "blob_field",
     "add_white_noise",
+    "gaussian_mask",
     "hermite_gaussian_1d",
     "hg_field",
     "random_symplectic_abcd",
@@ -66,6 +67,17 @@ def blob_field(nx: int, ny: int, seed: int, nblobs: int = 8,
         ey = np.exp(-((j - cj) ** 2) / (2 * w * w))
         out += (math.cos(psi) + 1j * math.sin(psi)) * (ex * ey)
     return out.astype(dtype)
+
+
+def gaussian_mask(nx: int, ny: int, sigma_frac: float = 0.25, tilt: float = 0.0,
+                  dtype=np.complex128) -> np.ndarray:
+    """A smooth filter for the NsLCT domain: a centred Gaussian window of
+    width sigma_frac * N (in samples) times a linear phase exp(j tilt p / N),
+    with p the centred row index."""
+    p = (np.arange(nx) - nx // 2)[:, None].astype(np.float64)
+    q = (np.arange(ny) - ny // 2)[None, :].astype(np.float64)
+    w = np.exp(-0.5 * ((p / (sigma_frac * nx)) ** 2 + (q / (sigma_frac * ny)) ** 2))
+    return (w * np.exp(1j * tilt * p / nx)).astype(dtype)
 
 
 def add_white_noise(field: np.ndarray, sigma: float, seed: int) -> np.ndarray:

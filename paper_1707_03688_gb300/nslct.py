@@ -32,6 +32,7 @@ NSLCT_H_LC = 0x1
 NSLCT_H_USER = 0x2
 NSLCT_H_LC_Y = 0x3
 NSLCT_FULL_CHAIN = 0x20
+NSLCT_CROP_OUTPUT = 0x40
 NSLCT_PROJECT_SP4 = 0x10
 NSLCT_PREC_FP32 = 0x000
 NSLCT_PREC_FP64 = 0x100
@@ -40,7 +41,8 @@ NSLCT_PREC_SPLIT_F16 = 0x200
 # every symbol include/nslct.h declares, in declaration order
 EXPORTED = (
     "nslct_plan", "nslct_plan_ex", "nslct_derive", "nslct_plan_params", "nslct_plan_info",
-    "nslct_forward", "nslct_inverse", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
+    "nslct_plan_padded", "nslct_plan_shape",
+    "nslct_forward", "nslct_forward_masked", "nslct_inverse", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
@@ -81,6 +83,9 @@ def load(path: str | None = None):
     sig = {
         "nslct_plan": (ctypes.c_int, [ctypes.POINTER(_VP), _PD, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_uint]),
         "nslct_plan_ex": (ctypes.c_int, [ctypes.POINTER(_VP), _PD, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_uint, _PD]),
+        "nslct_plan_padded": (ctypes.c_int, [ctypes.POINTER(_VP), _PD, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, _D, _D, ctypes.c_uint]),
+        "nslct_plan_shape": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int)] * 4),
         "nslct_derive": (ctypes.c_int, [_PD, ctypes.c_uint, _PD, _PD, _PD, _PD, _PD, _PD, _PD]),
         "nslct_plan_params": (ctypes.c_int, [_VP, ctypes.c_int, _PD, _PD, _PD, _PD]),
         "nslct_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -88,6 +93,7 @@ def load(path: str | None = None):
         "nslct_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_plan_passes": (ctypes.c_int, [_VP]),
+        "nslct_forward_masked": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
         "nslct_forward_pass": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
         "nslct_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "nslct_backward_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -179,6 +185,24 @@ def nslct_plan(abcd, nx: int, ny: int, dx: float, dy: float, flags: int = 0, h_u
     return handle.value
 
 
+def nslct_plan_padded(abcd, nx: int, ny: int, nx_pad: int, ny_pad: int, dx: float, dy: float,
+                      flags: int = 0) -> int:
+    """Plan on the zero-padded nx_pad x ny_pad grid for an nx x ny input (see include/nslct.h)."""
+    lib = load()
+    m, pm = _dbl(abcd, 16)
+    handle = _VP(0)
+    _check(lib.nslct_plan_padded(ctypes.byref(handle), pm, int(nx), int(ny), int(nx_pad), int(ny_pad), float(dx),
+                                 float(dy), ctypes.c_uint(flags)), "nslct_plan_padded")
+    return handle.value
+
+
+def nslct_plan_shape(plan: int):
+    """((input rows, cols), (output rows, cols)) of a plan."""
+    v = [ctypes.c_int(0) for _ in range(4)]
+    _check(load().nslct_plan_shape(_VP(plan), *[ctypes.byref(x) for x in v]), "nslct_plan_shape")
+    return (v[0].value, v[1].value), (v[2].value, v[3].value)
+
+
 def nslct_plan_params(plan: int, field: int = 0):
     lib = load()
     outs = [_out(4) for _ in range(4)]
@@ -222,6 +246,13 @@ def nslct_forward(plan: int, x, out, stream=None):
     """out = L x on `stream` (default: the current torch stream of out's device)."""
     _check(load().nslct_forward(_VP(plan), _VP(x.data_ptr()), _VP(out.data_ptr()), _stream_ptr(stream, out.device)),
            "nslct_forward")
+    return out
+
+
+def nslct_forward_masked(plan: int, x, mask, out, stream=None):
+    """out = mask * (L x), the mask multiplied in the last pass."""
+    _check(load().nslct_forward_masked(_VP(plan), _VP(x.data_ptr()), _VP(mask.data_ptr()), _VP(out.data_ptr()),
+                                       _stream_ptr(stream, out.device)), "nslct_forward_masked")
     return out
 
 
@@ -301,7 +332,7 @@ class Plan:
 
     def __init__(self, abcd, nx: int, ny: int, dx: float | None = None, dy: float | None = None,
                  method: str = "ha", h=None, project: bool = False, precision: str = "fp32",
-                 full_chain: bool = False):
+                 full_chain: bool = False, pad=None, crop: bool = False):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         self.dx = float(dx) if dx is not None else math.sqrt(2 * math.pi / self.nx)
@@ -324,7 +355,21 @@ class Plan:
         self.device = torch.cuda.current_device()
         self.flags = flags
         self.handle = None
-        self.handle = nslct_plan(abcd, self.nx, self.ny, self.dx, self.dy, flags, h_user=h)
+        if pad is None:
+            self.handle = nslct_plan(abcd, self.nx, self.ny, self.dx, self.dy, flags, h_user=h)
+        else:
+            if h is not None:
+                raise ValueError("padded plans choose H themselves")
+            self.handle = nslct_plan_padded(abcd, self.nx, self.ny, int(pad[0]), int(pad[1]), self.dx, self.dy,
+                                            flags | (NSLCT_CROP_OUTPUT if crop else 0))
+
+    @property
+    def in_shape(self):
+        return nslct_plan_shape(self.handle)[0]
+
+    @property
+    def out_shape(self):
+        return nslct_plan_shape(self.handle)[1]
 
     @classmethod
     def from_theta(cls, theta, nx: int, ny: int, h0=None, dx: float | None = None, dy: float | None = None,
@@ -370,20 +415,27 @@ class Plan:
     def info(self):
         return nslct_plan_info(self.handle)
 
-    def _prep(self, x, out):
+    def _prep(self, x, out, inverse=False):
         import torch
-        _check_field(x, self.nx, self.ny, self.dtype, self.device, "input")
+        (ir, ic), (orr, oc) = nslct_plan_shape(self.handle)
+        if inverse:
+            (ir, ic), (orr, oc) = (orr, oc), (ir, ic)
+        _check_field(x, ir, ic, self.dtype, self.device, "input")
         if out is None:
-            out = torch.empty_like(x)
-        _check_field(out, self.nx, self.ny, self.dtype, self.device, "output")
+            out = torch.empty((orr, oc), dtype=x.dtype, device=x.device)
+        _check_field(out, orr, oc, self.dtype, self.device, "output")
         return out
 
-    def forward(self, x, out=None, stream=None):
+    def forward(self, x, out=None, stream=None, mask=None):
+        """L x, or mask * (L x) with the mask fused into the last pass."""
         out = self._prep(x, out)
-        return nslct_forward(self.handle, x, out, stream)
+        if mask is None:
+            return nslct_forward(self.handle, x, out, stream)
+        _check_field(mask, out.shape[0], out.shape[1], self.dtype, self.device, "mask")
+        return nslct_forward_masked(self.handle, x, mask, out, stream)
 
     def inverse(self, x, out=None, stream=None):
-        out = self._prep(x, out)
+        out = self._prep(x, out, inverse=True)
         return nslct_inverse(self.handle, x, out, stream)
 
     def close(self):
@@ -460,7 +512,7 @@ class Batch:
                "nslct_batch_forward")
 
     def set_split(self, split: int):
-        """Fields with max(Nx, Ny) >= split run through their own fused passes."""
+        """Fields with min(Nx, Ny) >= split run through their own fused passes."""
         _check(load().nslct_batch_set_split(_VP(self.handle), int(split)), "nslct_batch_set_split")
 
     @property

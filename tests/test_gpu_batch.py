@@ -130,7 +130,7 @@ def test_batch_split_and_tune(N, batch_case):
     s.synchronize()
     close_to_ref()
     chosen, ms = b.tune(iters=2)
-    sizes = {max(nx, ny) for nx, ny in shapes} | {1 << 30}
+    sizes = {min(nx, ny) for nx, ny in shapes} | {1 << 30}
     assert chosen in sizes and b.split == chosen and ms > 0
     for o in outs:
         o.zero_()

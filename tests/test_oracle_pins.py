@@ -421,3 +421,88 @@ def test_printed_additivity(method):
         key = f"nmse_add_{gname}_{second}{first}_{method}"
         got = O.nmse(one, two)
         assert PV[key] / 1.5 < got < PV[key] * 1.5, (key, got)
+
+
+# ---------------------------------------------------------------- zero padding (Secs. 2.A, 5.A)
+
+
+def test_zero_padding_geometry_and_reversibility():
+    m = I.random_symplectic_abcd(91)
+    params = O.plan(m)
+    g = I.blob_field(10, 14, seed=91)
+    d = 0.6
+    # dN = 0 is the plain chain
+    np.testing.assert_array_equal(O.forward_padded(g, params, d, d, 10, 14), O.forward(g, params, d, d))
+    # placement keeps centred indices: the field's centre sample stays the grid's centre
+    gp = O.zero_pad(g, 16, 24)
+    assert gp[8, 12] == g[5, 7] and np.count_nonzero(gp) == np.count_nonzero(g)
+    np.testing.assert_array_equal(O.centre_crop(gp, 10, 14), g)
+    # the padded chain is still exactly invertible, zeros included
+    full = O.forward_padded(g, params, d, d, 16, 24)
+    assert full.shape == (16, 24)
+    back = O.inverse(full, params, d, d)
+    assert np.max(np.abs(back - gp)) < 1e-12
+    np.testing.assert_allclose(O.inverse_padded(full, params, d, d, 16, 24, 10, 14), g, atol=1e-12)
+    # the cropped output is the centre of the full one
+    np.testing.assert_array_equal(O.forward_padded(g, params, d, d, 16, 24, crop=True), O.centre_crop(full, 10, 14))
+
+
+def test_zero_padding_reduces_aliasing(reference_outputs):
+    """Sec. 5.A: g2 under M2 spreads beyond its 165 x 165 window and aliases
+    (NMSE 1.1e-3, printed); zero-padding the input to (165 + dN)^2 removes
+    it: against the direct method (Eq. Intro32) on each padded output grid the
+    NMSE falls below 1e-5 at dN = 20 and below 1e-6 at dN = 50."""
+    n_ref = int(PV["ref_grid_n"])
+    d_ref = PV["ref_grid_delta"]
+    m2 = O.project_sp4(PM["M2"])
+    g2 = I.hg_field([(2, 18), (14, 11)], 165, 0.2)
+    g2_fine = I.hg_field([(2, 18), (14, 11)], n_ref, d_ref)
+    params = O.plan(m2)
+    errs = [O.nmse(O.forward(g2, params, 0.2, 0.2), reference_outputs["g2"])]
+    for dn in (20, 50):
+        n = 165 + dn
+        ref = O.direct(g2_fine, m2, d_ref, d_ref, 0.2, 0.2, n, n)
+        errs.append(O.nmse(O.forward_padded(g2, params, 0.2, 0.2, n, n), ref))
+    assert errs[0] > 5e-4
+    assert errs[1] < 1e-5 and errs[2] < 1e-6
+    assert errs[0] > errs[1] > errs[2]
+
+
+# ---------------------------------------------------------------- filtering in two NsLCT domains (Sec. 5.B)
+
+
+def test_filter_pipelines_all_pass_identities():
+    """All-pass filters: Eq. Add04 returns the input exactly (each inverse is
+    exact), and since every chain is unitary the deviation of Eq. Add08 from
+    the input equals the additivity error of Eq. Add16 exactly."""
+    m1, m3 = I.random_symplectic_abcd(31), I.random_symplectic_abcd(32)
+    p1, p3, p31 = O.plan(m1), O.plan(m3), O.plan(m3 @ m1)
+    n, d = 24, float(np.sqrt(2 * np.pi / 24))
+    g = I.blob_field(n, n, seed=33, width_range=(1.5, 3.0))
+    ones = np.ones((n, n))
+    back = O.filter_two_domains(g, p1, p3, ones, ones, d, d)
+    assert np.max(np.abs(back - g)) < 1e-12
+    g8 = O.filter_two_domains_additive(g, p1, p3, p31, ones, ones, d, d)
+    e_add = O.nmse_add(g, p1, p3, p31, d, d)
+    assert e_add > 1e-8
+    assert abs(O.nmse(g8, g) - e_add) < 1e-9 * e_add
+
+
+def test_filter_pipelines_differ_by_the_additivity_error():
+    """With real filters the two pipelines differ by at most what the
+    additivity error allows: ||Add08 - Add04|| <= ||h3|| sqrt(NMSE_add-like)
+    (the composed inverse replaces two inverses; both unitary)."""
+    m1, m3 = O.project_sp4(PM["M1"]), O.project_sp4(PM["M3"])
+    p1, p3, p31 = O.plan(m1), O.plan(m3), O.plan(m3 @ m1)
+    g = I.hg_field([(1, 2), (3, 1)], 100, 0.25)
+    h1 = I.gaussian_mask(100, 100, 0.3, tilt=2.0)
+    h3 = I.gaussian_mask(100, 100, 0.4)
+    a = O.filter_two_domains(g, p1, p3, h1, h3, 0.25, 0.25)
+    b = O.filter_two_domains_additive(g, p1, p3, p31, h1, h3, 0.25, 0.25)
+    # Add08 - Add04 = (L31^-1 - L1^-1 L3^-1) y with y = h3 L3 h1 L1 g, and
+    # L31^-1 - L1^-1 L3^-1 = L31^-1 (I - L31 L1^-1 L3^-1): small when additive
+    y = h3 * O.forward(h1 * O.forward(g, p1, 0.25, 0.25), p3, 0.25, 0.25)
+    z = O.inverse(O.inverse(y, p3, 0.25, 0.25), p1, 0.25, 0.25)
+    rel = np.linalg.norm(O.forward(z, p31, 0.25, 0.25) - y) / np.linalg.norm(y)
+    assert abs(np.linalg.norm(b - a) / np.linalg.norm(y) - rel) < 1e-10
+    assert rel < 0.05
