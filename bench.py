@@ -41,6 +41,10 @@ FIELD_SEED = 2
 NOISE_SEED = 102
 ABCD_SEED0 = 200
 BYTES_PER_SAMPLE_PASS = 16        # read + write one complex64 per sample per pass
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per 4096^2 launch of the
+# current FP32 pass kernels (one full capture of one forward transform; row:
+# the mean of passes 1, 3, 5). Reset to None whenever those kernels change.
+NCU_TRAFFIC = {"pass_kernel_pair<4096,row>": 209.7e6, "pass_kernel_pair<4096,col>": 214.9e6}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
@@ -316,7 +320,8 @@ def run_gpu(args, world, rank, local):
                    "l2": "no flush: 16 distinct 128 MiB outputs per step, working set 2.1 GB > 126 MB L2"},
         "gpu_launches": args.steps * N_ABCD * npass,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": dom_name, "share": dom_share,
+                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom_name), "kernel": dom_name,
+                     "share": dom_share,
                      "peak_source": f"hbm_gbs ({peak_kind})",
                      "bytes_per_launch": bytes_launch, "avg_launch_ms": dom_ms},
         "chain": {"pass_ms": [round(v, 5) for v in pass_ms], "modelled_bytes_per_sample": npass * BYTES_PER_SAMPLE_PASS,
