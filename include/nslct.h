@@ -75,6 +75,19 @@ typedef struct CUstream_st* nslct_stream_t;  /* same type as cudaStream_t */
 #define NSLCT_FULL_CHAIN    0x20u
 /* nslct_plan_padded: return only the centred Nx x Ny region of the padded output. */
 #define NSLCT_CROP_OUTPUT   0x40u
+/* The CC-CM-CC-CM decomposition (Eq. CCCMCCCM16) instead of Eq. HA28: the
+ * chain CM^{Ca}, CC^{B1'}, CM^{Cb}, CC^{H1} with B1' = B - H1 D,
+ * Ca = B1'^-1 (A - H1 C - I), Cb = (D - I) B1'^-1. It is computed exactly as
+ * the inverse chain of the type-1 plan of M^-1 with H = -H1 (Eqs.
+ * CCCMCCCM20-30), and H1 is chosen by the same criterion (HA, LC or given):
+ * nslct_plan_params and nslct_derive then report the type-1 factors of M^-1
+ * (H = -H1), nslct_plan_info the caller's M with this flag set. */
+#define NSLCT_TYPE2         0x80u
+/* Eq. Reversible08: type 2 when tr(B) < 0, type 1 otherwise (tr B = 0, left
+ * open by the paper, counts as type 1); nslct_plan_info reports the choice
+ * through NSLCT_TYPE2. Neither flag combines with zero padding, batches or
+ * nslct_backward (NSLCT_E_UNSUPPORTED). */
+#define NSLCT_TYPE_BY_TRACE 0x1000u
 /* Arithmetic of the transform. */
 #define NSLCT_PREC_FP32     0x000u /* complex64 data, FP32 FFT arithmetic (default) */
 #define NSLCT_PREC_FP64     0x100u /* complex128 data, FP64 arithmetic throughout */

@@ -439,6 +439,99 @@ def inverse(big_g, params, dx: float, dy: float) -> np.ndarray:
     return x
 
 
+# --------------------------------------------------------------------------
+# CC-CM-CC-CM ("type 2") decomposition (Sec. 4.C) and the tr(B) rule of
+# Eq. Reversible08
+# --------------------------------------------------------------------------
+
+
+def decompose_type2(m, h1):
+    """Factors of Eq. CCCMCCCM16 for a symmetric H1:
+    B1' = B - H1 D and A1' = A - H1 C (Eq. CCCMCCCM23 before substitution),
+    Ca = B1'^-1 (A1' - I) (the CM applied first) and Cb = (D - I) B1'^-1 (the
+    CM applied third); the chain is CM^{Ca}, CC^{B1'}, CM^{Cb}, CC^{H1}.
+    B1' must be symmetric (the CC's chirp matrix), which constrains H1."""
+    a, b, c, d = split_abcd(m)
+    h1 = sym_part(h1)
+    eye = np.eye(2)
+    bp1 = b - h1 @ d
+    ap1 = a - h1 @ c
+    bpi = np.linalg.inv(bp1)
+    ca = bpi @ (ap1 - eye)
+    cb = (d - eye) @ bpi
+    return {"H1": h1, "Bp1": sym_part(bp1), "Ap1": ap1, "Ca": sym_part(ca), "Cb": sym_part(cb),
+            "Bp1_asym": float(abs(bp1[0, 1] - bp1[1, 0]))}
+
+
+def compose_factors_type2(p2):
+    """(I, H1; 0, I)(I, 0; Cb, I)(I, B1'; 0, I)(I, 0; Ca, I): the ABCD matrix
+    the type-2 chain stands for (CC^B <-> (I, B; 0, I), CM^C <-> (I, 0; C, I))."""
+    eye, z = np.eye(2), np.zeros((2, 2))
+    cc_m = lambda bb: np.block([[eye, bb], [z, eye]])
+    cm_m = lambda cc_: np.block([[eye, z], [cc_, eye]])
+    return cc_m(p2["H1"]) @ cm_m(p2["Cb"]) @ cc_m(p2["Bp1"]) @ cm_m(p2["Ca"])
+
+
+def ha_objective_type2(m, h1) -> float:
+    """The HA criterion carried to the type-2 chain: the product of the four
+    chirps' gamma factors, gamma(Ca) gamma(B1') gamma(Cb) gamma(H1)."""
+    p = decompose_type2(m, h1)
+    return gamma(p["Ca"]) * gamma(p["Bp1"]) * gamma(p["Cb"]) * gamma(p["H1"])
+
+
+def symplectic_inverse(m):
+    """(A, B; C, D)^-1 = (D^T, -B^T; -C^T, A^T) (Eq. CCCMCCCM20)."""
+    a, b, c, d = split_abcd(m)
+    return np.block([[d.T, -b.T], [-c.T, a.T]])
+
+
+def plan_type2(m, h1=None, method: str = "ha"):
+    """Type-2 factors for ABCD ``m``. H1 minimises the type-2 HA criterion;
+    since B1'(M, H1) = -B'(M^-1, -H1)^T (Eq. CCCMCCCM24) and likewise for the
+    other three chirps, and gamma depends on absolute values of a symmetric
+    matrix only, that criterion equals the type-1 one of M^-1 at -H1, so the
+    type-1 search on M^-1 is reused: H1 = -H(M^-1). ``method="lc"`` takes the
+    closed forms of Eqs. LC08/LC10 the same way."""
+    m = np.asarray(m, dtype=np.float64).reshape(4, 4)
+    if h1 is None:
+        mi = symplectic_inverse(m)
+        if method == "lc":
+            h = lc_h(mi)
+            if h is None:
+                h = ha_search(mi)
+        else:
+            h = ha_search(mi)
+        h1 = -h
+    return decompose_type2(m, h1)
+
+
+def forward_type2(g, p2, dx: float, dy: float) -> np.ndarray:
+    """Eq. CCCMCCCM16 applied right to left: CM^{Ca}, CC^{B1'}, CM^{Cb}, CC^{H1}."""
+    x = np.asarray(g, dtype=np.complex128)
+    x = cm(x, p2["Ca"], dx, dy)
+    x = cc(x, p2["Bp1"], dx, dy)
+    x = cm(x, p2["Cb"], dx, dy)
+    x = cc(x, p2["H1"], dx, dy)
+    return x
+
+
+def inverse_type2(big_g, p2, dx: float, dy: float) -> np.ndarray:
+    """The type-2 chain reversed with every chirp negated (its exact inverse)."""
+    x = np.asarray(big_g, dtype=np.complex128)
+    x = cc(x, -p2["H1"], dx, dy)
+    x = cm(x, -p2["Cb"], dx, dy)
+    x = cc(x, -p2["Bp1"], dx, dy)
+    x = cm(x, -p2["Ca"], dx, dy)
+    return x
+
+
+def uses_type2(m) -> bool:
+    """Eq. Reversible08: type 1 for tr(B) > 0, type 2 for tr(B) < 0; tr(B) = 0,
+    which the equation leaves open, is taken as type 1."""
+    _, b, _, _ = split_abcd(m)
+    return float(np.trace(b)) < 0.0
+
+
 def zero_pad(g, nx_pad: int, ny_pad: int) -> np.ndarray:
     """Zero-pad an Nx x Ny field to Nx_pad x Ny_pad (Sec. 2.A; Sec. 5.A pads
     the input to (N + dN) x (N + dN) against aliasing) keeping each sample at

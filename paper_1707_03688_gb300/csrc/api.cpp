@@ -97,7 +97,9 @@ int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   PassDesc d[5];
   bool cols[5];
-  const int npass = build_schedule(p, in, out, inverse, d, cols);
+  // a type-2 plan stores the type-1 factors of M^-1: its forward transform is
+  // that plan's inverse chain and vice versa
+  const int npass = build_schedule(p, in, out, inverse != (p->type2 != 0), d, cols);
   if (last >= npass) return NSLCT_E_ARG;
   if (mask) {
     if (reinterpret_cast<uintptr_t>(mask) & 15u) return NSLCT_E_ARG;
@@ -257,7 +259,35 @@ bool supported_length(int L) {
 extern "C" {
 
 // Host-only part of planning: validation, H choice and decomposition.
-static int derive(const double abcd[16], unsigned flags, const double* h_user, double m[16], Decomp* dc) {
+// Whether the plan runs the CC-CM-CC-CM chain (Eq. CCCMCCCM16): on request, or
+// by the tr(B) rule of Eq. Reversible08 (type 2 for tr B < 0; tr B = 0 is
+// left open by the equation and taken as type 1).
+static bool wants_type2(const double m[16], unsigned flags) {
+  if (flags & NSLCT_TYPE2) return true;
+  if (flags & NSLCT_TYPE_BY_TRACE) return m[2] + m[7] < 0.0;  // b11 + b22
+  return false;
+}
+
+// (A, B; C, D)^-1 = (D^T, -B^T; -C^T, A^T) (Eq. CCCMCCCM20), exact for symplectic M
+static void symplectic_inverse(const double m[16], double r[16]) {
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      r[i * 4 + j] = m[(j + 2) * 4 + (i + 2)];            // D^T
+      r[i * 4 + j + 2] = -m[j * 4 + (i + 2)];             // -B^T
+      r[(i + 2) * 4 + j] = -m[(j + 2) * 4 + i];           // -C^T
+      r[(i + 2) * 4 + j + 2] = m[j * 4 + i];              // A^T
+    }
+}
+
+static int derive_type1(const double m[16], unsigned flags, const double* h_user, Decomp* dc);
+
+// Validate (and optionally project) the caller's ABCD into m, choose H and
+// decompose. For type-2 plans the stored factors are the type-1 factors of
+// M^-1 with H = -H1: by Eqs. CCCMCCCM20-30 the type-2 chain of M with H1 is
+// exactly the inverse chain of that type-1 plan, and the type-2 HA criterion
+// (the gamma factors of its four chirps) equals the type-1 one of M^-1 at -H1.
+static int derive(const double abcd[16], unsigned flags, const double* h_user, double m[16], Decomp* dc,
+                  int* type2 = nullptr) {
   if (!abcd) return NSLCT_E_ARG;
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(abcd[i])) return NSLCT_E_ARG;
@@ -270,7 +300,20 @@ static int derive(const double abcd[16], unsigned flags, const double* h_user, d
     if (!project_sp4(abcd, m)) return NSLCT_E_NOT_SYMPLECTIC;
   }
   if (symplectic_residual(m) > 1e-9 * mmax * mmax) return NSLCT_E_NOT_SYMPLECTIC;
+  const bool t2 = wants_type2(m, flags);
+  if (type2) *type2 = t2 ? 1 : 0;
+  if (!t2) return derive_type1(m, flags, h_user, dc);
+  double mi[16];
+  symplectic_inverse(m, mi);
+  double hneg[4];
+  if (hsel == NSLCT_H_USER) {
+    for (int i = 0; i < 4; ++i) hneg[i] = -h_user[i];
+  }
+  return derive_type1(mi, flags, hsel == NSLCT_H_USER ? hneg : nullptr, dc);
+}
 
+static int derive_type1(const double m[16], unsigned flags, const double* h_user, Decomp* dc) {
+  const unsigned hsel = flags & NSLCT_H_MASK;
   Mat2 h{};
   int rc = NSLCT_OK;
   if (hsel == NSLCT_H_USER) {
@@ -311,12 +354,15 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   if (!supported_length(Nx) || !supported_length(Ny)) return NSLCT_E_SIZE;
   double m[16];
   Decomp dc{};
-  int rc = derive(abcd, flags, h_user, m, &dc);
+  int type2 = 0;
+  int rc = derive(abcd, flags, h_user, m, &dc, &type2);
   if (rc != NSLCT_OK) return rc;
 
   nslct_plan_s* p = new (std::nothrow) nslct_plan_s();
   if (!p) return NSLCT_E_NOMEM;
-  p->Nx = Nx; p->Ny = Ny; p->dx = dx; p->dy = dy; p->flags = flags;
+  p->Nx = Nx; p->Ny = Ny; p->dx = dx; p->dy = dy;
+  p->type2 = type2;
+  p->flags = (flags & ~NSLCT_TYPE2) | (type2 ? NSLCT_TYPE2 : 0u);
   p->prec = prec_flag == NSLCT_PREC_FP64 ? 1 : 0;
   p->mixed = prec_flag == NSLCT_PREC_SPLIT_F16 ? 1 : 0;
   std::memcpy(p->M, m, sizeof(m));
@@ -328,7 +374,8 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   fill_chirps(p);
   p->y_only_h = (p->prec == 0 && !(flags & NSLCT_FULL_CHAIN) && p->H[0] == 0.0 && p->H[1] == 0.0 && p->H[2] == 0.0)
                     ? 1 : 0;
-  p->has_theta = theta_from_abcd(p->M, p->theta) ? 1 : 0;
+  // theta gradients follow the type-1 chain of M only
+  p->has_theta = (!p->type2 && theta_from_abcd(p->M, p->theta)) ? 1 : 0;
   if (p->has_theta) chirp_jacobian(p->theta, p->H, p->jac);
 
   if (cudaGetDevice(&p->device) != cudaSuccess ||
@@ -370,7 +417,8 @@ int nslct_derive(const double abcd[16], unsigned flags, const double* h_user, do
                  double Bp[4], double C1[4], double C2[4], double* objective) {
   double m[16];
   Decomp dc{};
-  const int rc = derive(abcd, flags, h_user, m, &dc);
+  int type2 = 0;
+  const int rc = derive(abcd, flags, h_user, m, &dc, &type2);
   if (rc != NSLCT_OK) return rc;
   const Mat2* src[4] = {&dc.H, &dc.Bp, &dc.C1, &dc.C2};
   double* dst[4] = {H, Bp, C1, C2};
@@ -379,7 +427,11 @@ int nslct_derive(const double abcd[16], unsigned flags, const double* h_user, do
     dst[k][0] = src[k]->m00; dst[k][1] = src[k]->m01; dst[k][2] = src[k]->m10; dst[k][3] = src[k]->m11;
   }
   if (abcd_used) std::memcpy(abcd_used, m, sizeof(m));
-  if (objective) *objective = ha_objective(m, dc.H);
+  if (objective) {
+    double mi[16];
+    if (type2) symplectic_inverse(m, mi);
+    *objective = ha_objective(type2 ? mi : m, dc.H);
+  }
   return NSLCT_OK;
 }
 
@@ -390,6 +442,7 @@ int nslct_plan_theta(nslct_plan_t* out, const double theta[10], const double h0[
   if (!theta) return NSLCT_E_ARG;
   for (int i = 0; i < 10; ++i)
     if (!std::isfinite(theta[i])) return NSLCT_E_ARG;
+  if (flags & (NSLCT_TYPE2 | NSLCT_TYPE_BY_TRACE)) return NSLCT_E_UNSUPPORTED;
   const double det_l = theta[3] * theta[6] - theta[4] * theta[5];
   if (!(std::fabs(det_l) > 1e-12)) return NSLCT_E_ARG;
   double m[16];
@@ -417,6 +470,7 @@ int nslct_plan_padded(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, 
   if ((flags & NSLCT_H_MASK) == NSLCT_H_USER) return NSLCT_E_ARG;
   if (Nx < 2 || Ny < 2 || (Nx & 1) || (Ny & 1) || Nx > Nx_pad || Ny > Ny_pad) return NSLCT_E_ARG;
   const bool crop = (flags & NSLCT_CROP_OUTPUT) != 0;
+  if (flags & (NSLCT_TYPE2 | NSLCT_TYPE_BY_TRACE)) return NSLCT_E_UNSUPPORTED;
   int rc = nslct_plan_ex(out, abcd, Nx_pad, Ny_pad, dx, dy, flags & ~NSLCT_CROP_OUTPUT, nullptr);
   if (rc != NSLCT_OK) return rc;
   nslct_plan_s* p = *out;

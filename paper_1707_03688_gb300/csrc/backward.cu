@@ -143,7 +143,7 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
 extern "C" int nslct_backward(nslct_plan_t p, const void* grad_out, const void* y, void* grad_in, double* grad_theta,
                               double* grad_chirp, void* workspace, nslct_stream_t stream) {
   if (!p || !grad_out || !y || !grad_in) return NSLCT_E_ARG;
-  if (p->padded) return NSLCT_E_UNSUPPORTED;
+  if (p->padded || p->type2) return NSLCT_E_UNSUPPORTED;
   if (grad_theta && !p->has_theta) return NSLCT_E_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(grad_out) | reinterpret_cast<uintptr_t>(y) |
        reinterpret_cast<uintptr_t>(grad_in) | reinterpret_cast<uintptr_t>(workspace)) & 15u)

@@ -50,7 +50,7 @@ int partials_address(int device, double** out) {
 extern "C" int nslct_backward_noalloc(nslct_plan_t p, const void* grad_out, void* y_inout, void* grad_in,
                                       double* grad_theta, double* grad_chirp, nslct_stream_t stream) {
   if (!p || !grad_out || !y_inout || !grad_in) return NSLCT_E_ARG;
-  if (p->padded) return NSLCT_E_UNSUPPORTED;
+  if (p->padded || p->type2) return NSLCT_E_UNSUPPORTED;
   if (grad_theta && !p->has_theta) return NSLCT_E_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(grad_out) | reinterpret_cast<uintptr_t>(y_inout) |
        reinterpret_cast<uintptr_t>(grad_in)) & 15u)

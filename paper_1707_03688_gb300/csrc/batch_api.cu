@@ -24,6 +24,11 @@ struct nslct_batch_s {
   // nslct_batch_tune (default: every field batched)
   int split = 1 << 30;
   std::vector<int> Nx, Ny;
+  // the fields that run alone are spread over these streams (forked from and
+  // joined to the caller's stream by events), so their passes overlap
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
   bool bound = false;
   std::vector<const void*> in;
   std::vector<void*> out;
@@ -36,6 +41,11 @@ namespace {
 
 void free_batch(nslct_batch_s* b) {
   if (!b) return;
+  for (int k = 0; k < nslct_batch_s::kSide; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->d_descs) cudaFree(b->d_descs);
@@ -83,10 +93,17 @@ void drop_graph(nslct_batch_s* b) {
 }
 
 int enqueue(nslct_batch_s* b, cudaStream_t s) {
-  // the large fields first, each through its own fused passes
-  for (int f = 0; f < b->n; ++f) {
+  // the large fields, each through its own fused passes, round-robin over the
+  // side streams; the batched launches run on `s` meanwhile
+  int nalone = 0;
+  for (int f = 0; f < b->n; ++f) nalone += runs_alone(b, f) ? 1 : 0;
+  const int nside = std::min(nalone, (int)nslct_batch_s::kSide);
+  if (nside > 0 && cudaEventRecord(b->fork, s) != cudaSuccess) return NSLCT_E_CUDA;
+  for (int k = 0; k < nside; ++k)
+    if (cudaStreamWaitEvent(b->side[k], b->fork, 0) != cudaSuccess) return NSLCT_E_CUDA;
+  for (int f = 0, i = 0; f < b->n; ++f) {
     if (!runs_alone(b, f)) continue;
-    const int rc = nslct_forward(b->plans[f], b->in[f], b->out[f], s);
+    const int rc = nslct_forward(b->plans[f], b->in[f], b->out[f], b->side[i++ % nside]);
     if (rc != NSLCT_OK) return rc;
   }
   if (cudaMemsetAsync(b->d_counters, 0, 5 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
@@ -99,6 +116,9 @@ int enqueue(nslct_batch_s* b, cudaStream_t s) {
                                            : launch_batch_row(grid, descs, items, b->nitems[k], b->d_counters + k, s);
     if (rc != NSLCT_OK) return rc;
   }
+  for (int k = 0; k < nside; ++k)
+    if (cudaEventRecord(b->join[k], b->side[k]) != cudaSuccess || cudaStreamWaitEvent(s, b->join[k], 0) != cudaSuccess)
+      return NSLCT_E_CUDA;
   return NSLCT_OK;
 }
 
@@ -112,6 +132,7 @@ int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const 
   *out = nullptr;
   if (nfields <= 0 || !abcd || !Nx || !Ny || !dx || !dy) return NSLCT_E_ARG;
   if ((flags & NSLCT_PREC_MASK) != NSLCT_PREC_FP32) return NSLCT_E_UNSUPPORTED;
+  if (flags & (NSLCT_TYPE2 | NSLCT_TYPE_BY_TRACE)) return NSLCT_E_UNSUPPORTED;
   for (int f = 0; f < nfields; ++f)
     if (batch_panel_lines(Nx[f]) == 0 || batch_panel_lines(Ny[f]) == 0) return NSLCT_E_SIZE;
   nslct_batch_s* b = new (std::nothrow) nslct_batch_s();
@@ -130,6 +151,14 @@ int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const 
   }
   b->Nx.assign(Nx, Nx + nfields);
   b->Ny.assign(Ny, Ny + nfields);
+  bool ev_ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < nslct_batch_s::kSide && ev_ok; ++k)
+    ev_ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ev_ok) {
+    free_batch(b);
+    return NSLCT_E_CUDA;
+  }
   if (cudaMalloc(&b->d_descs, 5 * (size_t)nfields * sizeof(PassDesc)) != cudaSuccess ||
       cudaMalloc(&b->d_counters, 5 * sizeof(int)) != cudaSuccess) {
     free_batch(b);

@@ -332,6 +332,100 @@ struct LineFft {
   }
 };
 
+// Two FP32 fields' copies of the same line through one FFT schedule (the
+// adjoint's gradient and value paths): the exchanges move (a[e], b[e]) as one
+// 16-byte entry and each (correctly rounded) twiddle load serves both.
+template <int L, int P, int E_ = elems_per_thread(L)>
+struct LineFft2 {
+  static constexpr int E = E_;
+  static constexpr int T_LINE = L / E;
+  static constexpr int S = num_stages(L, E);
+  static constexpr int SH = pad_shift(E);
+  static __device__ __forceinline__ int sidx(int p, int e) { return padded_by<SH>(e) * P + p; }
+
+  template <int ST>
+  static __device__ __forceinline__ void stage(float2* a, float2* b, float4* sm, int t, int p,
+                                               const float2* __restrict__ tw) {
+    constexpr int RD = stage_radix(L, E, ST);
+    constexpr int NS = stage_ns(L, E, ST);
+    constexpr bool FIRST = (ST == 0);
+    constexpr bool LAST = (ST == S - 1);
+    constexpr int NB = E / RD;
+    if constexpr (!FIRST) {
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const float4 q = sm[sidx(p, t + T_LINE * s)];
+        a[s] = make_float2(q.x, q.y);
+        b[s] = make_float2(q.z, q.w);
+      }
+      if constexpr (!LAST) __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      float2 xa[RD], xb[RD];
+#pragma unroll
+      for (int r = 0; r < RD; ++r) {
+        xa[r] = a[u + r * NB];
+        xb[r] = b[u + r * NB];
+      }
+      const int j = t + u * T_LINE;
+      const int jm = j % NS;
+      if constexpr (NS > 1) {
+        float2 w[RD];
+        load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+#pragma unroll
+        for (int r = 1; r < RD; ++r) {
+          xa[r] = cmul<float>(xa[r], w[r]);
+          xb[r] = cmul<float>(xb[r], w[r]);
+        }
+      }
+      Dft<float, RD>::run(xa);
+      Dft<float, RD>::run(xb);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < RD; ++r) {
+          a[u + r * NB] = xa[r];
+          b[u + r * NB] = xb[r];
+        }
+      } else {
+        const int base = (j / NS) * NS * RD + jm;
+#pragma unroll
+        for (int r = 0; r < RD; ++r) sm[sidx(p, base + r * NS)] = make_float4(xa[r].x, xa[r].y, xb[r].x, xb[r].y);
+      }
+    }
+  }
+
+  template <int ST>
+  static __device__ __forceinline__ void stages(float2* a, float2* b, float4* sm, int t, int p,
+                                                const float2* __restrict__ tw) {
+    if constexpr (ST < S) {
+      stage<ST>(a, b, sm, t, p, tw);
+      stages<ST + 1>(a, b, sm, t, p, tw);
+    }
+  }
+
+  static __device__ __forceinline__ void run(float2* a, float2* b, float4* sm, int t, int p,
+                                             const float2* __restrict__ tw, bool inverse) {
+    if (inverse) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        a[s].y = -a[s].y;
+        b[s].y = -b[s].y;
+      }
+    }
+    if constexpr (S > 1) __syncthreads();
+    stages<0>(a, b, sm, t, p, tw);
+    if (inverse) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        a[s].y = -a[s].y;
+        b[s].y = -b[s].y;
+      }
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Split-precision tensor-core DFT-16 (the mixed mode, NSLCT_PREC_SPLIT_F16)
 //
@@ -1041,6 +1135,11 @@ bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P
 #ifndef NSLCT_PAIR_SHFL
 #define NSLCT_PAIR_SHFL 1
 #endif
+// column passes of the pair kernel: leave through the buffer by TMA stores (1)
+// or by 16-byte stores from registers with the next load issued first (0)
+#ifndef NSLCT_PAIR_COL_TMA_STORE
+#define NSLCT_PAIR_COL_TMA_STORE 1
+#endif
 
 template <int L> struct PairShape {
   static constexpr int E = 16;
@@ -1328,7 +1427,23 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
     __syncthreads();  // every thread has finished reading the buffer
     const int next = panel + gridDim.x;
 
-    if constexpr (COL) {
+    if constexpr (COL && !NSLCT_PAIR_COL_TMA_STORE) {
+      // next panel's load first, then 16-byte stores of (line0[e], line1[e]),
+      // one tile row of the column pair each
+      if (tid == 0 && next < npanels) {
+        fence_proxy_async();
+        pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
+      }
+      if (valid) {
+        float4* o4 = reinterpret_cast<float4*>(out);
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          const int e = t + T * s;
+          o4[((size_t)(e >> 1) * (2 * d.Ny) + (line0 >> 1) * 4 + (e & 1) * 2) >> 1] =
+              make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
+        }
+      }
+    } else if constexpr (COL) {
       // leave through the buffer: the box layout is (line0[e], line1[e]) per e
 #pragma unroll
       for (int s = 0; s < E; ++s)
@@ -1497,7 +1612,9 @@ template <typename R, int L> struct DualShape {
   static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);
   static constexpr int THREADS = T_LINE * P;
   static constexpr int XSM = P * (L + L / 16);
-  static constexpr size_t SMEM = (size_t)XSM * sizeof(cpx<R>) + 32 * 3 * sizeof(double);
+  // FP32: the two paths share each exchange (16-byte entries)
+  static constexpr size_t SMEM = (size_t)XSM * sizeof(cpx<R>) * (sizeof(R) == 4 ? 2 : 1) + 32 * 3 * sizeof(double);
+  static_assert(SMEM <= 227 * 1024, "adjoint kernel shared memory");
 };
 
 template <typename R, int L, bool COL>
@@ -1509,7 +1626,7 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
   constexpr int P = Sh::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
-  double* red = reinterpret_cast<double*>(smem_raw + (size_t)Sh::XSM * sizeof(cpx<R>));
+  double* red = reinterpret_cast<double*>(smem_raw + (size_t)Sh::XSM * sizeof(cpx<R>) * (sizeof(R) == 4 ? 2 : 1));
 
   const int tid = threadIdx.x;
   const int p = tid % P;
@@ -1534,8 +1651,12 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
     vy[s] = valid ? yin[k] : mk<R>((R)0, (R)0);
   }
   if (d.t1 != kNone) {
-    LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t1 == kInv);
-    LineFft<R, L, P, E, false, true>::run(vy, sm, t, p, tw, d.t1 == kInv);
+    if constexpr (sizeof(R) == 4) {
+      LineFft2<L, P, E>::run(vg, vy, reinterpret_cast<float4*>(sm), t, p, tw, d.t1 == kInv);
+    } else {
+      LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t1 == kInv);
+      LineFft<R, L, P, E, false, true>::run(vy, sm, t, p, tw, d.t1 == kInv);
+    }
   }
   if (accumulate) {
     // coordinates as in apply_chirp
@@ -1594,8 +1715,12 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
     }
   }
   if (d.t2 != kNone) {
-    LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t2 == kInv);
-    LineFft<R, L, P, E, false, true>::run(vy, sm, t, p, tw, d.t2 == kInv);
+    if constexpr (sizeof(R) == 4) {
+      LineFft2<L, P, E>::run(vg, vy, reinterpret_cast<float4*>(sm), t, p, tw, d.t2 == kInv);
+    } else {
+      LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t2 == kInv);
+      LineFft<R, L, P, E, false, true>::run(vy, sm, t, p, tw, d.t2 == kInv);
+    }
   }
   __syncthreads();  // in-place: all loads of the panel happened before any store
   if (valid) {

@@ -102,6 +102,7 @@ struct nslct_plan_s {
   int prec;            // 0 = fp32, 1 = fp64
   int mixed;           // NSLCT_PREC_SPLIT_F16: FP32 data, split-FP16 tensor-core DFT-16 stages
   int y_only_h;        // H = (0,0;0,h): CC^H acts along y only and the chain runs in 3 passes
+  int type2;           // CC-CM-CC-CM chain: the factors below are the type-1 ones of M^-1
   int device;
   double M[16];        // the (possibly projected) ABCD matrix
   double H[4], Bp[4], C1[4], C2[4];

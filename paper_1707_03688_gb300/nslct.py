@@ -33,6 +33,8 @@ NSLCT_H_USER = 0x2
 NSLCT_H_LC_Y = 0x3
 NSLCT_FULL_CHAIN = 0x20
 NSLCT_CROP_OUTPUT = 0x40
+NSLCT_TYPE2 = 0x80
+NSLCT_TYPE_BY_TRACE = 0x1000
 NSLCT_PROJECT_SP4 = 0x10
 NSLCT_PREC_FP32 = 0x000
 NSLCT_PREC_FP64 = 0x100
@@ -326,13 +328,15 @@ class Plan:
     """One ABCD matrix on one Nx x Ny field, on the current CUDA device.
 
     ``method``: "ha" (Eq. HA24), "lc" (Eqs. LC08/LC10) or an explicit 2x2 ``h``.
+    ``decomposition``: "type1" (CM-CC-CM-CC, Eq. HA28), "type2" (CC-CM-CC-CM,
+    Eq. CCCMCCCM16) or "trace" (the tr(B) rule of Eq. Reversible08).
     ``precision``: "fp32" (complex64) or "fp64" (complex128).
     ``dx``/``dy`` default to sqrt(2 pi / N) (the paper's sampling condition).
     """
 
     def __init__(self, abcd, nx: int, ny: int, dx: float | None = None, dy: float | None = None,
                  method: str = "ha", h=None, project: bool = False, precision: str = "fp32",
-                 full_chain: bool = False, pad=None, crop: bool = False):
+                 full_chain: bool = False, pad=None, crop: bool = False, decomposition: str = "type1"):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         self.dx = float(dx) if dx is not None else math.sqrt(2 * math.pi / self.nx)
@@ -342,6 +346,7 @@ class Plan:
             flags |= NSLCT_PROJECT_SP4
         if full_chain:
             flags |= NSLCT_FULL_CHAIN
+        flags |= {"type1": 0, "type2": NSLCT_TYPE2, "trace": NSLCT_TYPE_BY_TRACE}[decomposition]
         if precision == "fp64":
             flags |= NSLCT_PREC_FP64
             self.dtype = torch.complex128

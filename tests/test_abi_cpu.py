@@ -133,3 +133,22 @@ def test_plan_rejects_bad_sizes_without_touching_the_gpu(lib):
     with pytest.raises(N.NslctError) as exc:
         N.nslct_plan(m, 64, 64, -1.0, 0.3)
     assert exc.value.code == N.NSLCT_E_ARG
+
+
+def test_derive_type2_is_type1_of_the_inverse(lib):
+    """NSLCT_TYPE2 reports the type-1 factors of M^-1 with H = -H1, H1 as good
+    as the oracle's type-2 choice; the tr(B) rule picks type 2 exactly for tr B < 0."""
+    for s in range(4):
+        m = I.random_symplectic_abcd(70 + s)
+        d2 = N.nslct_derive(m, flags=N.NSLCT_TYPE2)
+        p2 = O.plan_type2(m)
+        # both searches minimise the same criterion (near-ties may pick nearby H)
+        assert O.ha_objective_type2(m, -d2["H"]) <= O.ha_objective_type2(m, p2["H1"]) * (1 + 1e-6)
+        mi = O.symplectic_inverse(m)
+        p1 = O.decompose(mi, d2["H"])
+        for k in ("Bp", "C1", "C2"):
+            np.testing.assert_allclose(d2[k], p1[k], atol=1e-9)
+        np.testing.assert_allclose(d2["abcd"], m, atol=0)
+        dt = N.nslct_derive(m, flags=N.NSLCT_TYPE_BY_TRACE)
+        ref = d2 if O.uses_type2(m) else N.nslct_derive(m)
+        np.testing.assert_allclose(dt["H"], ref["H"], atol=0)

@@ -141,7 +141,8 @@ def test_fp32_paper_matrices(N, name, method):
 
 
 SHAPES = [(8, 8), (12, 16), (16, 12), (48, 64), (64, 48), (96, 192), (192, 96), (384, 24),
-          (24, 384), (768, 128), (128, 1536), (1536, 64), (2048, 32), (32, 4096), (256, 1024)]
+          (24, 384), (768, 128), (128, 1536), (1536, 64), (2048, 32), (32, 4096), (256, 1024),
+          (4096, 8), (8, 4096)]
 
 
 @pytest.mark.parametrize("nx,ny", SHAPES)
@@ -258,3 +259,23 @@ def test_4096_full_oracle(N, field_4096):
     out = _gpu(plan, field_4096)
     ref = _oracle(plan, field_4096)
     assert O.rel_l2(out, ref) < TOL32
+
+
+def test_zero_field_gives_exact_zeros(N):
+    """The chain is linear: a zero field maps to exact zeros (no NaN from the
+    chirps or the twiddle powers), in every precision."""
+    for precision, dt in (("fp32", torch.complex64), ("fp64", torch.complex128), ("mixed", torch.complex64)):
+        plan = _plan(N, I.random_symplectic_abcd(3), 256, 512, precision=precision)
+        x = torch.zeros(256, 512, dtype=dt, device="cuda")
+        y = plan.forward(x)
+        z = plan.inverse(x)
+        torch.cuda.synchronize()
+        assert int(torch.count_nonzero(y)) == 0 and int(torch.count_nonzero(z)) == 0
+
+
+def test_fp64_4096_full_oracle(N, field_4096):
+    """The largest size in complex128 against the direct-sum oracle."""
+    plan = _plan(N, I.random_symplectic_abcd(201), 4096, 4096, precision="fp64")
+    out = _gpu(plan, field_4096)
+    ref = _oracle(plan, field_4096)
+    assert O.rel_l2(out, ref) < tol64(4096, 4096)

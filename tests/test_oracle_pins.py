@@ -506,3 +506,45 @@ def test_filter_pipelines_differ_by_the_additivity_error():
     rel = np.linalg.norm(O.forward(z, p31, 0.25, 0.25) - y) / np.linalg.norm(y)
     assert abs(np.linalg.norm(b - a) / np.linalg.norm(y) - rel) < 1e-10
     assert rel < 0.05
+
+
+# ---------------------------------------------------------------- CC-CM-CC-CM decomposition (Sec. 4.C)
+
+
+def test_type2_decomposition_identities():
+    """Eq. CCCMCCCM16's factors multiply back to M; by Eqs. CCCMCCCM20-30 the
+    type-2 chain of M^-1 with H1 = -H is the type-1 inverse chain of M; the
+    type-2 criterion of M at H1 is the type-1 criterion of M^-1 at -H1; the
+    chain is exactly reversible and reduces to the 2D DFT of Eq. BasicDFT16."""
+    n = 16
+    d = float(np.sqrt(2 * np.pi / n))
+    g = I.blob_field(n, n, seed=8, width_range=(1.5, 3.0))
+    for s in range(3):
+        m = I.random_symplectic_abcd(80 + s)
+        p2 = O.plan_type2(m)
+        assert p2["Bp1_asym"] < 1e-12
+        assert np.max(np.abs(O.compose_factors_type2(p2) - m)) < 1e-12
+        mi = O.symplectic_inverse(m)
+        assert np.max(np.abs(mi @ m - np.eye(4))) < 1e-12
+        assert abs(O.ha_objective_type2(m, p2["H1"]) - O.ha_objective(mi, -p2["H1"])) < 1e-9
+        p1 = O.plan(m)
+        dual = O.forward_type2(g, O.decompose_type2(mi, -p1["H"]), d, d)
+        assert np.max(np.abs(dual - O.inverse(g, p1, d, d))) < 1e-12
+        back = O.inverse_type2(O.forward_type2(g, p2, d, d), p2, d, d)
+        assert np.max(np.abs(back - g)) < 1e-12
+    z, e = np.zeros((2, 2)), np.eye(2)
+    dft = np.block([[z, e], [-e, z]])
+    out = O.forward_type2(g, O.plan_type2(dft), d, d)
+    ref = d * d / (2j * np.pi) * np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(g)))
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_trace_rule():
+    """Eq. Reversible08 picks type 2 exactly when tr(B) < 0; M and M^-1 have
+    opposite traces of B, so forward and inverse use different types."""
+    for s in range(6):
+        m = I.random_symplectic_abcd(90 + s)
+        tb = np.trace(m[:2, 2:])
+        assert O.uses_type2(m) == (tb < 0)
+        if tb != 0:
+            assert O.uses_type2(O.symplectic_inverse(m)) != O.uses_type2(m)
