@@ -19,90 +19,99 @@ namespace nslct {
 #define NSLCT_BATCH_LENGTHS(X) \
   X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(96) X(192) X(384) X(768) X(1536)
 
-template <int L> struct BShape {
+// Two CTA sizes: 512 threads (one CTA per SM, every length) and 256 threads
+// (two CTAs per SM with independent barriers, lines up to 2048: a panel needs
+// at least two lines of L/E threads each).
+template <int L, int TH> struct BShape {
   static constexpr int E = elems_per_thread(L);  // the plans' tw16 tables
   static constexpr int T_LINE = L / E;
-  static constexpr int THREADS = 512;
-  static constexpr int P = THREADS / T_LINE;   // lines per panel
-  static_assert(P >= 2 && P % 2 == 0, "panel width");
+  static constexpr int THREADS = TH;
+  static constexpr int P = TH / T_LINE;        // lines per panel
+  static constexpr bool ok = P >= 2 && P % 2 == 0 && P * T_LINE == TH;
   static constexpr int XSM = P * (L + L / 16);
   static constexpr int STG_ROW = P * (L + 8);  // row-major rows are padded in staging
   static constexpr int STG_TILED = P * L;
 };
 
-constexpr int kBatchThreads = 512;
-
 // exchange-buffer and staging-buffer entries for the largest need among the lengths
+template <int TH>
 __host__ __device__ constexpr int batch_xsm() {
   int m = 0;
-#define NSLCT_BSM(LL) m = BShape<LL>::XSM > m ? BShape<LL>::XSM : m;
+#define NSLCT_BSM(LL) \
+  if (BShape<LL, TH>::ok && BShape<LL, TH>::XSM > m) m = BShape<LL, TH>::XSM;
   NSLCT_BATCH_LENGTHS(NSLCT_BSM)
 #undef NSLCT_BSM
   return m;
 }
+template <int TH>
 __host__ __device__ constexpr int batch_stg() {
   int m = 0;
-#define NSLCT_BSM(LL) m = BShape<LL>::STG_ROW > m ? BShape<LL>::STG_ROW : m;
+#define NSLCT_BSM(LL) \
+  if (BShape<LL, TH>::ok && BShape<LL, TH>::STG_ROW > m) m = BShape<LL, TH>::STG_ROW;
   NSLCT_BATCH_LENGTHS(NSLCT_BSM)
 #undef NSLCT_BSM
   return m;
 }
-constexpr int kBatchXsm = batch_xsm();
-constexpr size_t kBatchSmem = (size_t)(batch_xsm() + batch_stg()) * sizeof(float2);
-static_assert(kBatchSmem <= 227 * 1024, "batched kernel shared memory");
+template <int TH> constexpr size_t batch_smem() { return (size_t)(batch_xsm<TH>() + batch_stg<TH>()) * sizeof(float2); }
+static_assert(batch_smem<512>() <= 227 * 1024, "batched kernel shared memory");
+static_assert(batch_smem<256>() <= 113 * 1024, "two 256-thread batched CTAs per SM");
 
+// lines per panel for line length L with TH-thread CTAs (0: not handled)
+template <int TH>
 __host__ __device__ constexpr int batch_lines_of(int L) {
 #define NSLCT_BP(LL) \
-  if (L == LL) return BShape<LL>::P;
+  if (L == LL) return BShape<LL, TH>::ok ? BShape<LL, TH>::P : 0;
   NSLCT_BATCH_LENGTHS(NSLCT_BP)
 #undef NSLCT_BP
   return 0;
 }
 
-template <int L, bool COL>
+template <int L, bool COL, int TH>
 __device__ __forceinline__ int bstg_index(int p, int e, int tiled) {
-  constexpr int P = BShape<L>::P;
+  constexpr int P = BShape<L, TH>::P;
   if (COL) return (e >> 1) * (2 * P) + (p >> 1) * 4 + (e & 1) * 2 + (p & 1);
   if (tiled) return (p >> 1) * (2 * L) + (e >> 1) * 4 + (p & 1) * 2 + (e & 1);
   return p * (L + 8) + e;
 }
 
 // Issue the 16-byte copies of one panel (every thread takes part).
-template <int L, bool COL>
+template <int L, bool COL, int TH>
 __device__ __forceinline__ void bstage_panel(float2* stg, const PassDesc& d, int panel) {
-  constexpr int P = BShape<L>::P;
+  constexpr int P = BShape<L, TH>::P;
   constexpr int CHUNKS = P * L / 2;
   const float2* __restrict__ in = reinterpret_cast<const float2*>(d.in);
   const int first = panel * P;
   if (COL) {
     const int tiles_valid = min(P, d.Ny - first) / 2;
-    for (int c = threadIdx.x; c < CHUNKS; c += kBatchThreads) {
+    for (int c = threadIdx.x; c < CHUNKS; c += TH) {
       const int a = c / P, k = c % P;
       if ((k >> 1) < tiles_valid)
         cp_async16(stg + a * (2 * P) + k * 2, in + (size_t)a * (2 * d.Ny) + (first >> 1) * 4 + k * 2);
     }
   } else if (d.in_tiled) {
     const int rows_valid = min(P, d.Nx - first);
-    for (int c = threadIdx.x; c < CHUNKS; c += kBatchThreads) {
+    for (int c = threadIdx.x; c < CHUNKS; c += TH) {
       const int q = c / L, k = c % L;
       if (2 * q < rows_valid) cp_async16(stg + q * (2 * L) + k * 2, in + (size_t)((first >> 1) + q) * (2 * L) + k * 2);
     }
   } else {
     constexpr int CPR = L / 2;
     const int rows_valid = min(P, d.Nx - first);
-    for (int c = threadIdx.x; c < CHUNKS; c += kBatchThreads) {
+    for (int c = threadIdx.x; c < CHUNKS; c += TH) {
       const int q = c / CPR, k = c % CPR;
       if (q < rows_valid) cp_async16(stg + q * (L + 8) + k * 2, in + (size_t)(first + q) * L + k * 2);
     }
   }
 }
 
-template <bool COL>
+template <bool COL, int TH>
 __device__ __forceinline__ void bstage_any(float2* stg, const PassDesc& d, int panel) {
   const int L = COL ? d.Nx : d.Ny;
   switch (L) {
 #define NSLCT_BCASE(LL) \
-  case LL: bstage_panel<LL, COL>(stg, d, panel); break;
+  case LL:                                                \
+    if constexpr (BShape<LL, TH>::ok) bstage_panel<LL, COL, TH>(stg, d, panel); \
+    break;
     NSLCT_BATCH_LENGTHS(NSLCT_BCASE)
 #undef NSLCT_BCASE
     default: break;
@@ -112,11 +121,11 @@ __device__ __forceinline__ void bstage_any(float2* stg, const PassDesc& d, int p
 
 // Compute one item whose panel sits in `stg`; prefetch `next` (if any) into
 // `stg` once the panel is in registers.
-template <int L, bool COL>
+template <int L, bool COL, int TH>
 __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* stg, float2* xs,
                                          const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items,
                                          int next, int nitems) {
-  using Sh = BShape<L>;
+  using Sh = BShape<L, TH>;
   constexpr int E = Sh::E;
   constexpr int T_LINE = Sh::T_LINE;
   constexpr int P = Sh::P;
@@ -128,11 +137,11 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
   const bool valid = line < nlines;
   float2 v[E];
 #pragma unroll
-  for (int s = 0; s < E; ++s) v[s] = stg[bstg_index<L, COL>(p, t + T_LINE * s, d.in_tiled)];
+  for (int s = 0; s < E; ++s) v[s] = stg[bstg_index<L, COL, TH>(p, t + T_LINE * s, d.in_tiled)];
   __syncthreads();  // staging consumed
   if (next < nitems) {
     const BatchItem it = items[next];
-    bstage_any<COL>(stg, descs[it.field], it.panel);
+    bstage_any<COL, TH>(stg, descs[it.field], it.panel);
   }
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   if (d.t1 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t1 == kInv);
@@ -157,20 +166,20 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
 
 // One pass of the batch. descs[f] is field f's descriptor for this pass;
 // items[0..nitems) the work list; *counter must be 0 at launch.
-template <bool COL>
-__global__ void __launch_bounds__(kBatchThreads, 1)
+template <bool COL, int TH>
+__global__ void __launch_bounds__(TH, TH <= 256 ? 2 : 1)
 batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item[2];
   float2* xs = reinterpret_cast<float2*>(smem_raw);
   // the exchange buffer (sized for the largest need) comes first, staging after it
-  float2* stg = xs + kBatchXsm;
+  float2* stg = xs + batch_xsm<TH>();
   if (threadIdx.x == 0) s_item[0] = atomicAdd(counter, 1);
   __syncthreads();
   int cur = s_item[0];
   if (cur < nitems) {
     const BatchItem it = items[cur];
-    bstage_any<COL>(stg, descs[it.field], it.panel);
+    bstage_any<COL, TH>(stg, descs[it.field], it.panel);
   }
   while (cur < nitems) {
     if (threadIdx.x == 0) s_item[1] = atomicAdd(counter, 1);
@@ -181,8 +190,10 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
     const PassDesc& d = descs[it.field];
     const int L = COL ? d.Nx : d.Ny;
     switch (L) {
-#define NSLCT_BCASE(LL) \
-  case LL: bprocess<LL, COL>(d, it.panel, stg, xs, descs, items, next, nitems); break;
+#define NSLCT_BCASE(LL)                                                                 \
+  case LL:                                                                              \
+    if constexpr (BShape<LL, TH>::ok) bprocess<LL, COL, TH>(d, it.panel, stg, xs, descs, items, next, nitems); \
+    break;
       NSLCT_BATCH_LENGTHS(NSLCT_BCASE)
 #undef NSLCT_BCASE
       default: break;
@@ -194,18 +205,22 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
 }
 
 template <bool COL>
-inline int launch_batch(int grid, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
-                        cudaStream_t s) {
-  batch_pass_kernel<COL><<<grid, kBatchThreads, kBatchSmem, s>>>(descs, items, nitems, counter);
+inline int launch_batch(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems,
+                        int* counter, cudaStream_t s) {
+  if (threads == 256)
+    batch_pass_kernel<COL, 256><<<grid, 256, batch_smem<256>(), s>>>(descs, items, nitems, counter);
+  else
+    batch_pass_kernel<COL, 512><<<grid, 512, batch_smem<512>(), s>>>(descs, items, nitems, counter);
   return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
 }
 
 template <bool COL>
 inline int prepare_batch() {
-  return cudaFuncSetAttribute(batch_pass_kernel<COL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kBatchSmem) == cudaSuccess
-             ? NSLCT_OK
-             : NSLCT_E_CUDA;
+  const bool ok = cudaFuncSetAttribute(batch_pass_kernel<COL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_smem<256>()) == cudaSuccess &&
+                  cudaFuncSetAttribute(batch_pass_kernel<COL, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_smem<512>()) == cudaSuccess;
+  return ok ? NSLCT_OK : NSLCT_E_CUDA;
 }
 
 }  // namespace nslct

@@ -23,6 +23,7 @@ struct nslct_batch_s {
   // kernels (nslct_forward) instead of the batched launches; chosen by
   // nslct_batch_tune (default: every field batched)
   int split = 1 << 30;
+  int threads = 512;   // CTA size of the batched kernels: 256 when every line is <= 2048
   std::vector<int> Nx, Ny;
   // the fields that run alone are spread over these streams (forked from and
   // joined to the caller's stream by events), so their passes overlap
@@ -74,7 +75,7 @@ int build_items(nslct_batch_s* b) {
     for (int f : order) {
       const int L = col ? b->Nx[f] : b->Ny[f];
       const int lines = col ? b->Ny[f] : b->Nx[f];
-      const int P = batch_panel_lines(L);
+      const int P = batch_panel_lines(L, b->threads);
       for (int panel = 0; panel * P < lines; ++panel) all.push_back(BatchItem{f, panel});
     }
     b->nitems[k] = (int)all.size() - b->item_off[k];
@@ -109,11 +110,12 @@ int enqueue(nslct_batch_s* b, cudaStream_t s) {
   if (cudaMemsetAsync(b->d_counters, 0, 5 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
   for (int k = 0; k < 5; ++k) {
     if (b->nitems[k] == 0) continue;
-    const int grid = std::min(b->nitems[k], b->num_sms);
+    const int grid = std::min(b->nitems[k], (b->threads == 256 ? 2 : 1) * b->num_sms);
     const PassDesc* descs = b->d_descs + (size_t)k * b->n;
     const BatchItem* items = b->d_items + b->item_off[k];
-    const int rc = chain_pass_is_column(k) ? launch_batch_col(grid, descs, items, b->nitems[k], b->d_counters + k, s)
-                                           : launch_batch_row(grid, descs, items, b->nitems[k], b->d_counters + k, s);
+    const int rc = chain_pass_is_column(k)
+                       ? launch_batch_col(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s)
+                       : launch_batch_row(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s);
     if (rc != NSLCT_OK) return rc;
   }
   for (int k = 0; k < nside; ++k)
@@ -134,10 +136,20 @@ int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const 
   if ((flags & NSLCT_PREC_MASK) != NSLCT_PREC_FP32) return NSLCT_E_UNSUPPORTED;
   if (flags & (NSLCT_TYPE2 | NSLCT_TYPE_BY_TRACE)) return NSLCT_E_UNSUPPORTED;
   for (int f = 0; f < nfields; ++f)
-    if (batch_panel_lines(Nx[f]) == 0 || batch_panel_lines(Ny[f]) == 0) return NSLCT_E_SIZE;
+    if (batch_panel_lines(Nx[f], 512) == 0 || batch_panel_lines(Ny[f], 512) == 0) return NSLCT_E_SIZE;
   nslct_batch_s* b = new (std::nothrow) nslct_batch_s();
   if (!b) return NSLCT_E_NOMEM;
   b->n = nfields;
+#ifndef NSLCT_BATCH_THREADS
+#define NSLCT_BATCH_THREADS 256
+#endif
+  b->threads = 512;
+  if (NSLCT_BATCH_THREADS == 256) {
+    bool all256 = true;
+    for (int f = 0; f < nfields && all256; ++f)
+      all256 = batch_panel_lines(Nx[f], 256) != 0 && batch_panel_lines(Ny[f], 256) != 0;
+    if (all256) b->threads = 256;
+  }
   if (cudaGetDevice(&b->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
     free_batch(b);

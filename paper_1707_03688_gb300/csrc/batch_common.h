@@ -10,12 +10,13 @@ struct BatchItem {
   int panel;  // panel of that field's pass
 };
 
-// Lines per panel of the batched kernels for line length L (0 if unsupported).
-int batch_panel_lines(int L);
+// Lines per panel of the batched kernels for line length L with `threads`-thread
+// CTAs (256 or 512; 0 if that CTA size does not handle L).
+int batch_panel_lines(int L, int threads);
 
-int launch_batch_row(int grid, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
+int launch_batch_row(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
                      cudaStream_t s);
-int launch_batch_col(int grid, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
+int launch_batch_col(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
                      cudaStream_t s);
 int prepare_batch_row();
 int prepare_batch_col();

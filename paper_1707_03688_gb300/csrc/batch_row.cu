@@ -2,10 +2,12 @@
 #include "batch.cuh"
 
 namespace nslct {
-int batch_panel_lines(int L) { return batch_lines_of(L); }
-int launch_batch_row(int grid, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
+int batch_panel_lines(int L, int threads) {
+  return threads == 256 ? batch_lines_of<256>(L) : threads == 512 ? batch_lines_of<512>(L) : 0;
+}
+int launch_batch_row(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
                      cudaStream_t s) {
-  return launch_batch<false>(grid, descs, items, nitems, counter, s);
+  return launch_batch<false>(grid, threads, descs, items, nitems, counter, s);
 }
 int prepare_batch_row() { return prepare_batch<false>(); }
 }  // namespace nslct

@@ -1605,10 +1605,15 @@ namespace nslct {
 // these into d loss / d chirp entries. One panel per CTA; partial sums per CTA
 // go to `partials[blockIdx.x][3]` (FP64), reduced later in a fixed order.
 // ---------------------------------------------------------------------------
+#ifndef NSLCT_DUAL_THREADS
+#define NSLCT_DUAL_THREADS 256
+#endif
 template <typename R, int L> struct DualShape {
   static constexpr int E = elems_per_thread(L);  // the plan's tw16 tables
   static constexpr int T_LINE = L / E;
-  static constexpr int P0 = 512 / T_LINE;
+  // NSLCT_DUAL_THREADS-thread CTAs (at least two lines): 256 gives twice the
+  // CTAs of 512 and lets two share an SM
+  static constexpr int P0 = NSLCT_DUAL_THREADS / T_LINE;
   static constexpr int P = P0 < 2 ? 2 : (P0 > 32 ? 32 : P0);
   static constexpr int THREADS = T_LINE * P;
   static constexpr int XSM = P * (L + L / 16);
@@ -1618,7 +1623,7 @@ template <typename R, int L> struct DualShape {
 };
 
 template <typename R, int L, bool COL>
-__global__ void __launch_bounds__(DualShape<R, L>::THREADS, 1)
+__global__ void __launch_bounds__(DualShape<R, L>::THREADS, DualShape<R, L>::THREADS <= 256 ? 2 : 1)
 dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, int accumulate) {
   using Sh = DualShape<R, L>;
   constexpr int E = Sh::E;

@@ -346,11 +346,15 @@ int choose_h_lc_y(const double* m, Mat2* h_out) {
 
 // ---------------------------------------------------------------- fixed-point chirps
 
-// fractional part of x as a Q0.64 fraction of a turn
+// x mod 1 as a Q0.64 fraction of a turn, in two's complement. The fraction
+// is split off with trunc (x - trunc(x) is exact) and scaled as it is; taking
+// x - floor(x) instead would compute 1 + x for negative x and round away the
+// low bits of a small coefficient, which a^2 ~ 4e6 then multiplies.
 uint64_t turns_q64(double x) {
-  double f = x - std::floor(x);  // exact for finite x, in [0, 1)
-  if (!(f >= 0.0) || f >= 1.0) f = 0.0;
-  return (uint64_t)std::ldexp(f, 64);
+  if (!std::isfinite(x)) return 0;
+  const double xf = x - std::trunc(x);  // exact, |xf| < 1, sign of x
+  if (xf >= 0.0) return (uint64_t)std::ldexp(xf, 64);
+  return (uint64_t)0 - (uint64_t)std::ldexp(-xf, 64);
 }
 
 // chirp exp(j/2 (c11 a^2 da^2 + 2 c12 a b da db + c22 b^2 db^2)) in turns
