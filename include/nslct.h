@@ -111,7 +111,8 @@ typedef struct CUstream_st* nslct_stream_t;  /* same type as cudaStream_t */
  *            path supports.
  *   dx, dy   sampling intervals (> 0). The paper's condition for the DFT case
  *            is dx^2 = 2 pi / Nx, dy^2 = 2 pi / Ny (Sec. 2.B).
- *   flags    NSLCT_H_*, NSLCT_PROJECT_SP4, NSLCT_PREC_*.
+ *   flags    NSLCT_H_*, NSLCT_PROJECT_SP4, NSLCT_FULL_CHAIN, NSLCT_TYPE2 or
+ *            NSLCT_TYPE_BY_TRACE, NSLCT_PREC_*.
  *
  * All derivation (symplectic check/projection, the H criterion of Eq. HA24 or
  * the closed form of Eqs. LC08/LC10, B', D', C1, C2, fixed-point chirp
@@ -151,18 +152,22 @@ int nslct_plan_params(nslct_plan_t plan, int field, double H[4], double Bp[4],
                       double C1[4], double C2[4]);
 
 /*
- * nslct_plan_info -- field size, precision flag and the projected ABCD the plan
- * uses (abcd may be NULL).
+ * nslct_plan_info -- field size (the padded grid for padded plans), the plan's
+ * flags (NSLCT_TYPE2 set when the type-2 chain is in use) and the projected
+ * ABCD the plan uses (abcd may be NULL).
  */
 int nslct_plan_info(nslct_plan_t plan, int* Nx, int* Ny, unsigned* flags, double abcd[16]);
 
 /*
- * nslct_forward -- out = L in, the NsDLCT of Eq. HA28.
- *   in, out  device buffers of Nx*Ny complex elements (see "Data" above).
- *            in == out (in-place) is allowed; otherwise they must not overlap.
- *            `out` doubles as the chain's intermediate storage, so no
- *            workspace is allocated.
- * Five kernel passes are enqueued on `stream`.
+ * nslct_forward -- out = L in, the NsDLCT of Eq. HA28 (of Eq. CCCMCCCM16 for
+ * type-2 plans).
+ *   in, out  device buffers of Nx*Ny complex elements (see "Data" above),
+ *            16-byte aligned; padded plans: the shapes of nslct_plan_shape.
+ *            in == out (in-place) is allowed except for padded plans;
+ *            otherwise they must not overlap. `out` doubles as the chain's
+ *            intermediate storage, so no workspace is allocated (padded plans
+ *            with a smaller output use their own).
+ * nslct_plan_passes() kernel passes (5, or 3) are enqueued on `stream`.
  */
 int nslct_forward(nslct_plan_t plan, const void* in, void* out, nslct_stream_t stream);
 
@@ -257,7 +262,8 @@ int nslct_forward_pass(nslct_plan_t plan, int pass, const void* in, void* out, n
  * inverse chain next to grad_out, so nothing is stored by nslct_forward. On the
  * first call with gradients the plan also allocates a small buffer of per-CTA
  * partial sums. Calls on one plan that overlap on the GPU share those buffers
- * and race. All device pointers must be 16-byte aligned.
+ * and race. All device pointers must be 16-byte aligned. Padded and type-2
+ * plans are not supported (NSLCT_E_UNSUPPORTED).
  */
 int nslct_backward(nslct_plan_t plan, const void* grad_out, const void* y, void* grad_in,
                    double* grad_theta, double* grad_chirp, void* workspace, nslct_stream_t stream);
