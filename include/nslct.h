@@ -205,6 +205,20 @@ int nslct_plan_padded(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, 
 int nslct_plan_shape(nslct_plan_t plan, int* in_rows, int* in_cols, int* out_rows, int* out_cols);
 
 /*
+ * nslct_forward_many / nslct_inverse_many -- the transform (or its inverse) of
+ * nbatch fields with the same plan: field b is read at in + b * in_stride and
+ * written at out + b * out_stride (strides in complex elements, >= Nx*Ny
+ * when nbatch > 1, each field 16-byte aligned; in == out needs equal
+ * strides). For FP32 plans whose lines are 256..4096 points each pass is one
+ * launch over the whole batch; other plans launch each pass once per field.
+ * Padded plans: NSLCT_E_UNSUPPORTED. Otherwise as nslct_forward / nslct_inverse.
+ */
+int nslct_forward_many(nslct_plan_t plan, int nbatch, const void* in, long long in_stride, void* out,
+                       long long out_stride, nslct_stream_t stream);
+int nslct_inverse_many(nslct_plan_t plan, int nbatch, const void* in, long long in_stride, void* out,
+                       long long out_stride, nslct_stream_t stream);
+
+/*
  * nslct_forward_masked -- out = mask .* (L in): the forward transform followed
  * by a pointwise filter in the NsLCT domain (the H1, H3 of Eqs. Add04/Add08),
  * multiplied in the last pass before the store, so it costs one read of the
@@ -267,6 +281,19 @@ int nslct_forward_pass(nslct_plan_t plan, int pass, const void* in, void* out, n
  */
 int nslct_backward(nslct_plan_t plan, const void* grad_out, const void* y, void* grad_in,
                    double* grad_theta, double* grad_chirp, void* workspace, nslct_stream_t stream);
+
+/*
+ * nslct_backward_many -- nslct_backward for nbatch fields of one plan whose
+ * loss is the sum of per-field terms (a batch with shared ABCD parameters):
+ * grad_out, y, grad_in (and workspace, if given) hold nbatch fields `stride`
+ * elements apart (>= Nx*Ny when nbatch > 1, 16-byte aligned fields);
+ * grad_in gets each field's L^H grad_out, and grad_theta / grad_chirp the
+ * gradients summed over the batch. Each dual pass is one launch over the
+ * batch. The plan's own workspace and partial-sum buffer grow to the batch.
+ */
+int nslct_backward_many(nslct_plan_t plan, int nbatch, long long stride, const void* grad_out, const void* y,
+                        void* grad_in, double* grad_theta, double* grad_chirp, void* workspace,
+                        nslct_stream_t stream);
 
 /*
  * nslct_plan_theta -- plan for M(theta) (see nslct_backward) with H = h0 moved

@@ -1,7 +1,8 @@
 """torch.autograd wrapper around nslct_forward / nslct_backward.
 
 ``nslct_transform(x, theta, h0)`` returns y = L_theta x for a complex field x
-(Nx, Ny) and the 10 ABCD parameters theta (see include/nslct.h,
+(Nx, Ny), or a batch (B, Nx, Ny) transformed field by field, and the 10 ABCD
+parameters theta (see include/nslct.h,
 nslct_plan_theta); gradients flow to x and to theta through the library's
 adjoint kernels (nslct_backward). PyTorch only holds memory and streams.
 """
@@ -17,7 +18,8 @@ class NsLCTFunction(torch.autograd.Function):
     def forward(ctx, x, theta, h0, precision):
         ctx.theta_device = theta.device
         ctx.theta_dtype = theta.dtype
-        plan = N.Plan.from_theta(theta.detach().cpu().double().numpy(), x.shape[0], x.shape[1],
+        # a field (Nx, Ny) or a batch (B, Nx, Ny) sharing theta
+        plan = N.Plan.from_theta(theta.detach().cpu().double().numpy(), x.shape[-2], x.shape[-1],
                                  h0=None if h0 is None else h0.detach().cpu().double().numpy(), precision=precision)
         y = plan.forward(x.contiguous())
         ctx.plan = plan

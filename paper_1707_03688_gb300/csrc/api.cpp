@@ -81,12 +81,26 @@ void free_plan(nslct_plan_s* p) {
 }
 
 int launch(const nslct_plan_s* p, bool col, const PassDesc& d, cudaStream_t s) {
+  if (d.nbatch > 1 && !(p->prec == 0 && !p->mixed && pair_kernel_length(col ? d.Nx : d.Ny))) {
+    // a kernel without a batch dimension: one launch per field
+    const size_t esz = p->prec == 1 ? 16 : 8;
+    for (int b = 0; b < d.nbatch; ++b) {
+      PassDesc e = d;
+      e.nbatch = 1;
+      e.in = static_cast<const char*>(d.in) + (size_t)b * d.in_bstride * esz;
+      e.out = static_cast<char*>(d.out) + (size_t)b * d.out_bstride * esz;
+      const int rc = p->prec == 1 ? launch_pass_f64(col, e, s) : launch_pass_f32(col, e, s);
+      if (rc != NSLCT_OK) return rc;
+    }
+    return NSLCT_OK;
+  }
   return p->prec == 1 ? launch_pass_f64(col, d, s) : launch_pass_f32(col, d, s);
 }
 
 // Enqueue passes [first, last] of the forward (or inverse) chain.
 int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, bool inverse, int first = 0,
-              int last = 4, const void* mask = nullptr) {
+              int last = 4, const void* mask = nullptr, int nbatch = 1, long long in_stride = 0,
+              long long out_stride = 0) {
   if (!p || !in || !out || first < 0 || last > 4 || first > last) return NSLCT_E_ARG;
   // 16-byte copies need 16-byte aligned fields
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return NSLCT_E_ARG;
@@ -104,6 +118,15 @@ int run_chain(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream, 
   if (mask) {
     if (reinterpret_cast<uintptr_t>(mask) & 15u) return NSLCT_E_ARG;
     d[npass - 1].post_mask = mask;
+  }
+  if (nbatch > 1) {
+    // the first pass reads the caller's input; every other access is to the
+    // output (the intermediate lives there)
+    for (int k = 0; k < npass; ++k) {
+      d[k].nbatch = nbatch;
+      d[k].in_bstride = k == 0 ? in_stride : out_stride;
+      d[k].out_bstride = out_stride;
+    }
   }
   for (int k = first; k <= last; ++k) {
     const int rc = launch(p, cols[k], d[k], s);
@@ -537,6 +560,33 @@ int nslct_inverse(nslct_plan_t p, const void* in, void* out, nslct_stream_t stre
 }
 
 int nslct_plan_passes(nslct_plan_t p) { return !p ? 0 : (p->y_only_h ? 3 : 5); }
+
+// Field strides of a same-plan batch: at least one field, 16-byte aligned
+// fields, and in-place only with equal strides.
+static int check_many(nslct_plan_t p, int nbatch, const void* in, long long in_stride, const void* out,
+                      long long out_stride) {
+  if (!p || nbatch < 1 || p->padded) return p && p->padded ? NSLCT_E_UNSUPPORTED : NSLCT_E_ARG;
+  const long long n = (long long)p->Nx * p->Ny;
+  const size_t esz = p->prec == 1 ? 16 : 8;
+  if (nbatch > 1 && (in_stride < n || out_stride < n)) return NSLCT_E_ARG;
+  if (((size_t)in_stride * esz) % 16 || ((size_t)out_stride * esz) % 16) return NSLCT_E_ARG;
+  if (in == out && in_stride != out_stride) return NSLCT_E_ARG;
+  return NSLCT_OK;
+}
+
+int nslct_forward_many(nslct_plan_t p, int nbatch, const void* in, long long in_stride, void* out,
+                       long long out_stride, nslct_stream_t stream) {
+  const int rc = check_many(p, nbatch, in, in_stride, out, out_stride);
+  if (rc != NSLCT_OK) return rc;
+  return run_chain(p, in, out, stream, false, 0, nslct_plan_passes(p) - 1, nullptr, nbatch, in_stride, out_stride);
+}
+
+int nslct_inverse_many(nslct_plan_t p, int nbatch, const void* in, long long in_stride, void* out,
+                       long long out_stride, nslct_stream_t stream) {
+  const int rc = check_many(p, nbatch, in, in_stride, out, out_stride);
+  if (rc != NSLCT_OK) return rc;
+  return run_chain(p, in, out, stream, true, 0, nslct_plan_passes(p) - 1, nullptr, nbatch, in_stride, out_stride);
+}
 
 int nslct_forward_masked(nslct_plan_t p, const void* in, const void* mask, void* out, nslct_stream_t stream) {
   if (!mask) return NSLCT_E_ARG;

@@ -80,7 +80,8 @@ int dual_rows(const nslct_plan_s* p, int L, int nlines) {
 // Shared by nslct_backward and its variants: the five dual passes (writing
 // per-CTA sums to `partials`, `stride` rows per pass) and the finalisation.
 int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, void* grad_in, double* grad_theta,
-                        double* grad_chirp, void* ws, double* partials, int stride, cudaStream_t s) {
+                        double* grad_chirp, void* ws, double* partials, int stride, cudaStream_t s, int nbatch,
+                        long long fstride) {
   const double nn = (double)p->Nx * (double)p->Ny;
   const double ccs = -1.0 / nn;
   PassDesc base{};
@@ -106,6 +107,10 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
     x.scale_only = (!x.has_chirp && x.scale != 1.0) ? 1 : 0;
     x.num_sms = p->num_sms;
     x.err = p->err;
+    // a same-plan batch: every array is nbatch fields fstride elements apart,
+    // and the CTA sums of all fields add into the (shared) parameter gradients
+    x.nbatch = nbatch;
+    x.in_bstride = x.out_bstride = fstride;
   }
   const bool cols[5] = {false, true, false, true, false};
   const bool want = grad_theta || grad_chirp;
@@ -114,7 +119,7 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
     const int acc = (want && k < 4) ? 1 : 0;
     if (acc) {
       const int L = cols[k] ? p->Nx : p->Ny;
-      f.nblk[k] = dual_rows(p, L, cols[k] ? p->Ny : p->Nx);
+      f.nblk[k] = (nbatch > 1 ? nbatch : 1) * dual_rows(p, L, cols[k] ? p->Ny : p->Nx);
       if (f.nblk[k] < 0 || f.nblk[k] > stride) return NSLCT_E_SIZE;
     }
     const void* in_y = k == 0 ? y : ws;
@@ -140,34 +145,58 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
   return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
 }
 
-extern "C" int nslct_backward(nslct_plan_t p, const void* grad_out, const void* y, void* grad_in, double* grad_theta,
-                              double* grad_chirp, void* workspace, nslct_stream_t stream) {
-  if (!p || !grad_out || !y || !grad_in) return NSLCT_E_ARG;
+// nslct_backward over a same-plan batch of nbatch fields fstride elements apart
+// (one field: nbatch = 1). The value-path workspace and the CTA partial sums
+// are the plan's unless the caller passes a workspace; both grow on demand.
+static int backward_batch(nslct_plan_t p, int nbatch, long long fstride, const void* grad_out, const void* y,
+                          void* grad_in, double* grad_theta, double* grad_chirp, void* workspace,
+                          nslct_stream_t stream) {
+  if (!p || !grad_out || !y || !grad_in || nbatch < 1) return NSLCT_E_ARG;
   if (p->padded || p->type2) return NSLCT_E_UNSUPPORTED;
   if (grad_theta && !p->has_theta) return NSLCT_E_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(grad_out) | reinterpret_cast<uintptr_t>(y) |
        reinterpret_cast<uintptr_t>(grad_in) | reinterpret_cast<uintptr_t>(workspace)) & 15u)
     return NSLCT_E_ARG;
+  const size_t esz = p->prec == 1 ? 16 : 8;
+  const long long n = (long long)p->Nx * p->Ny;
+  if (nbatch > 1 && (fstride < n || ((size_t)fstride * esz) % 16)) return NSLCT_E_ARG;
+  const long long span = nbatch > 1 ? (long long)(nbatch - 1) * fstride + n : n;  // elements a batch array covers
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return NSLCT_E_CUDA;
   if (prev != p->device && cudaSetDevice(p->device) != cudaSuccess) return NSLCT_E_CUDA;
   int rc = NSLCT_OK;
-  const size_t esz = p->prec == 1 ? 16 : 8;
-  // plan-owned scratch, made on first use: the value-path field (unless the
-  // caller passes one) and the per-CTA partial sums
-  if (!workspace && !p->ws) {
-    if (cudaMalloc(&p->ws, esz * (size_t)p->Nx * p->Ny) != cudaSuccess) { p->ws = nullptr; rc = NSLCT_E_NOMEM; }
+  if (!workspace && p->ws_elems < span) {
+    if (p->ws) cudaFree(p->ws);
+    p->ws = nullptr;
+    p->ws_elems = 0;
+    if (cudaMalloc(&p->ws, esz * (size_t)span) != cudaSuccess) { p->ws = nullptr; rc = NSLCT_E_NOMEM; }
+    else p->ws_elems = span;
   }
-  if (rc == NSLCT_OK && !p->partials) {
-    p->partials_stride = (p->Nx > p->Ny ? p->Nx : p->Ny) / 2 + 1;
-    if (cudaMalloc(&p->partials, sizeof(double) * 3 * 4 * (size_t)p->partials_stride) != cudaSuccess) {
+  const int rows = nbatch * ((p->Nx > p->Ny ? p->Nx : p->Ny) / 2 + 1);
+  if (rc == NSLCT_OK && (!p->partials || p->partials_stride < rows)) {
+    if (p->partials) cudaFree(p->partials);
+    p->partials = nullptr;
+    p->partials_stride = rows;
+    if (cudaMalloc(&p->partials, sizeof(double) * 3 * 4 * (size_t)rows) != cudaSuccess) {
       p->partials = nullptr;
+      p->partials_stride = 0;
       rc = NSLCT_E_NOMEM;
     }
   }
   if (rc == NSLCT_OK)
     rc = nslct_backward_impl(p, grad_out, y, grad_in, grad_theta, grad_chirp, workspace ? workspace : p->ws,
-                             p->partials, p->partials_stride, reinterpret_cast<cudaStream_t>(stream));
+                             p->partials, p->partials_stride, reinterpret_cast<cudaStream_t>(stream), nbatch, fstride);
   if (prev != p->device) cudaSetDevice(prev);
   return rc;
+}
+
+extern "C" int nslct_backward(nslct_plan_t p, const void* grad_out, const void* y, void* grad_in, double* grad_theta,
+                              double* grad_chirp, void* workspace, nslct_stream_t stream) {
+  return backward_batch(p, 1, 0, grad_out, y, grad_in, grad_theta, grad_chirp, workspace, stream);
+}
+
+extern "C" int nslct_backward_many(nslct_plan_t p, int nbatch, long long stride, const void* grad_out, const void* y,
+                                   void* grad_in, double* grad_theta, double* grad_chirp, void* workspace,
+                                   nslct_stream_t stream) {
+  return backward_batch(p, nbatch, stride, grad_out, y, grad_in, grad_theta, grad_chirp, workspace, stream);
 }

@@ -19,7 +19,8 @@
 
 // defined in backward.cu
 int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, void* grad_in, double* grad_theta,
-                        double* grad_chirp, void* ws, double* partials, int stride, cudaStream_t s);
+                        double* grad_chirp, void* ws, double* partials, int stride, cudaStream_t s, int nbatch,
+                        long long fstride);
 
 namespace {
 
@@ -64,7 +65,7 @@ extern "C" int nslct_backward_noalloc(nslct_plan_t p, const void* grad_out, void
   int rc = partials_address(p->device, &partials);
   if (rc == NSLCT_OK)
     rc = nslct_backward_impl(p, grad_out, y_inout, grad_in, grad_theta, grad_chirp, y_inout, partials, kNoallocRows,
-                             reinterpret_cast<cudaStream_t>(stream));
+                             reinterpret_cast<cudaStream_t>(stream), 1, 0);
   if (prev != p->device) cudaSetDevice(prev);
   return rc;
 }

@@ -171,6 +171,10 @@ __global__ void __launch_bounds__(TH, TH <= 256 ? 2 : 1)
 batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item[2];
+  // the current item's descriptor, copied once per item: every thread reads
+  // many of its fields, which from global memory cost a load latency each
+  __shared__ __align__(16) PassDesc s_desc;
+  static_assert(sizeof(PassDesc) % 4 == 0, "descriptor copy by words");
   float2* xs = reinterpret_cast<float2*>(smem_raw);
   // the exchange buffer (sized for the largest need) comes first, staging after it
   float2* stg = xs + batch_xsm<TH>();
@@ -187,7 +191,13 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
     __syncthreads();
     const int next = s_item[1];
     const BatchItem it = items[cur];
-    const PassDesc& d = descs[it.field];
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(descs + it.field);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_desc);
+      for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += TH) dst[w] = src[w];
+    }
+    __syncthreads();
+    const PassDesc& d = s_desc;
     const int L = COL ? d.Nx : d.Ny;
     switch (L) {
 #define NSLCT_BCASE(LL)                                                                 \

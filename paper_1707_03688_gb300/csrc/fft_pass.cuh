@@ -869,6 +869,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, const void* src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(map), "r"(x),
+               "r"(y), "r"(z), "r"(smem_u32(src))
+               : "memory");
+}
 __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
                "r"(bytes)
@@ -1110,6 +1122,10 @@ pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __
 // pairs (2 Ny complex, 16 Ny bytes apart), the box is 2P complex wide (P/2
 // tiles) and up to 256 row pairs tall. Complex64 values are 8-byte elements.
 bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P);
+// The same as a 3D map over a batch of nbatch fields bstride elements apart
+// (the batch index is the third coordinate).
+bool encode_column_map_batched(CUtensorMap* map, const void* base, int Nx, int Ny, int P, int nbatch,
+                               long long bstride);
 
 // ---------------------------------------------------------------------------
 // v4 (FP32, power-of-two lines of 256..4096): line-pair kernel.
@@ -1128,9 +1144,7 @@ bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P
 // so two CTAs share an SM and overlap each other's loads, stores and barriers.
 // Waits are bounded as in v3.
 // ---------------------------------------------------------------------------
-#ifndef NSLCT_PAIR
-#define NSLCT_PAIR 1
-#endif
+// (NSLCT_PAIR: see internal.h)
 // row passes of the pair kernel: 16-byte tiled loads and stores with a lane-pair shuffle
 #ifndef NSLCT_PAIR_SHFL
 #define NSLCT_PAIR_SHFL 1
@@ -1260,7 +1274,7 @@ template <int L> struct PairFft {
 // (4 complex wide) per pair; row pairs: one or two 1D bulk copies per pair.
 template <int L, bool COL>
 __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, const CUtensorMap* map,
-                                                const PassDesc& d, int first, uint64_t* bar) {
+                                                const PassDesc& d, int first, uint64_t* bar, int b) {
   using Sh = PairShape<L>;
   const int nlines = COL ? d.Ny : d.Nx;
   const int pairs = min(Sh::G, (nlines - first) >> 1);
@@ -1270,7 +1284,7 @@ __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, con
     mbar_arrive_expect_tx(bar, (uint32_t)(pairs * rows * 4 * sizeof(float2)));
     for (int g = 0; g < pairs; ++g)
       for (int y0 = 0; y0 < rows; y0 += box)
-        tma_load_2d(reinterpret_cast<float2*>(x + g * Sh::LS) + y0 * 4, map, 2 * (first + 2 * g), y0, bar);
+        tma_load_3d(reinterpret_cast<float2*>(x + g * Sh::LS) + y0 * 4, map, 2 * (first + 2 * g), y0, b, bar);
   } else if (d.in_tiled) {
     mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)));
     for (int g = 0; g < pairs; ++g)
@@ -1316,9 +1330,11 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
   const int g = tid / T;
   const int t = tid % T;
   const int nlines = COL ? d.Ny : d.Nx;
-  const int npanels = (nlines + P - 1) / P;
-  const float2* in = reinterpret_cast<const float2*>(d.in);
-  float2* out = reinterpret_cast<float2*>(d.out);
+  const int npf = (nlines + P - 1) / P;                 // panels per field
+  const int nb = d.nbatch > 1 ? d.nbatch : 1;
+  const int npanels = npf * nb;                          // over the whole batch
+  const float2* in0 = reinterpret_cast<const float2*>(d.in);
+  float2* out0 = reinterpret_cast<float2*>(d.out);
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   float4* xg = xs + g * Sh::LS;                 // this thread's pair region
   float2* xg2 = reinterpret_cast<float2*>(xg);
@@ -1326,11 +1342,18 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_fence_init();
-    if ((int)blockIdx.x < npanels) pair_load_panel<L, COL>(xs, in, &map_in, d, blockIdx.x * P, bar);
+    if ((int)blockIdx.x < npanels) {
+      const int b0 = blockIdx.x / npf;
+      pair_load_panel<L, COL>(xs, in0 + b0 * d.in_bstride, &map_in, d, (blockIdx.x % npf) * P, bar, b0);
+    }
   }
   __syncthreads();
   int it = 0;
-  for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x, ++it) {
+  for (int gp = blockIdx.x; gp < npanels; gp += gridDim.x, ++it) {
+    const int bf = gp / npf;                             // field of the batch
+    const int panel = gp % npf;
+    const float2* in = in0 + bf * d.in_bstride;
+    float2* out = out0 + bf * d.out_bstride;
     const int first = panel * P;
     const int line0 = first + 2 * g;
     const bool valid = line0 < nlines;          // lines come in pairs (even counts)
@@ -1425,14 +1448,15 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       }
     }
     __syncthreads();  // every thread has finished reading the buffer
-    const int next = panel + gridDim.x;
+    const int next = gp + gridDim.x;
+    const int nbf = next / npf;                          // the next panel's field
 
     if constexpr (COL && !NSLCT_PAIR_COL_TMA_STORE) {
       // next panel's load first, then 16-byte stores of (line0[e], line1[e]),
       // one tile row of the column pair each
       if (tid == 0 && next < npanels) {
         fence_proxy_async();
-        pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
+        pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf);
       }
       if (valid) {
         float4* o4 = reinterpret_cast<float4*>(out);
@@ -1456,15 +1480,16 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         const int box = col_box_rows(rows);
         for (int q = 0; q < pairs; ++q)
           for (int y0 = 0; y0 < rows; y0 += box)
-            tma_store_2d(&map_out, 2 * (first + 2 * q), y0, reinterpret_cast<float2*>(xs + q * Sh::LS) + y0 * 4);
+            tma_store_3d(&map_out, 2 * (first + 2 * q), y0, bf, reinterpret_cast<float2*>(xs + q * Sh::LS) + y0 * 4);
         bulk_commit();
         bulk_wait_read_all();  // the buffer is free again
-        if (next < npanels) pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
+        if (next < npanels)
+          pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf);
       }
     } else {
       if (tid == 0 && next < npanels) {
         fence_proxy_async();
-        pair_load_panel<L, COL>(xs, in, &map_in, d, next * P, bar);
+        pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf);
       }
       if (!d.out_tiled && d.pad_out) {
         // zero padding: store the output region alone
@@ -1537,9 +1562,11 @@ inline int launch_one(const PassDesc& d, cudaStream_t s) {
     }
     if constexpr (NSLCT_PAIR && is_pow2(L) && L >= 256) {
       using Sh = PairShape<L>;
-      const int npanels = (nlines + Sh::P - 1) / Sh::P;
-      const int blocks = npanels < 2 * d.num_sms ? npanels : 2 * d.num_sms;
-      if (COL && (!encode_column_map(&mi, d.in, d.Nx, d.Ny, 2) || !encode_column_map(&mo, d.out, d.Nx, d.Ny, 2)))
+      const int nb = d.nbatch > 1 ? d.nbatch : 1;
+      const long long npanels = (long long)((nlines + Sh::P - 1) / Sh::P) * nb;
+      const int blocks = npanels < 2 * d.num_sms ? (int)npanels : 2 * d.num_sms;
+      if (COL && (!encode_column_map_batched(&mi, d.in, d.Nx, d.Ny, 2, nb, d.in_bstride) ||
+                  !encode_column_map_batched(&mo, d.out, d.Nx, d.Ny, 2, nb, d.out_bstride)))
         return NSLCT_E_CUDA;
       pass_kernel_pair<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, mi, mo);
       return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
@@ -1637,12 +1664,15 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
   const int p = tid % P;
   const int t = tid / P;
   const int nlines = COL ? d.Ny : d.Nx;
-  const int line = blockIdx.x * P + p;
+  // same-plan batches: CTA b * (CTAs per field) + k takes panel k of field b
+  const int cpf = (nlines + P - 1) / P;
+  const int bf = blockIdx.x / cpf;
+  const int line = (blockIdx.x % cpf) * P + p;
   const bool valid = line < nlines;
-  const cpx<R>* __restrict__ gin = reinterpret_cast<const cpx<R>*>(d.in);
-  const cpx<R>* __restrict__ yin = reinterpret_cast<const cpx<R>*>(in_y);
-  cpx<R>* gout = reinterpret_cast<cpx<R>*>(d.out);
-  cpx<R>* yout = reinterpret_cast<cpx<R>*>(out_y);
+  const cpx<R>* __restrict__ gin = reinterpret_cast<const cpx<R>*>(d.in) + bf * d.in_bstride;
+  const cpx<R>* __restrict__ yin = reinterpret_cast<const cpx<R>*>(in_y) + bf * d.in_bstride;
+  cpx<R>* gout = reinterpret_cast<cpx<R>*>(d.out) + bf * d.out_bstride;
+  cpx<R>* yout = reinterpret_cast<cpx<R>*>(out_y) + bf * d.out_bstride;
   const cpx<R>* __restrict__ tw = reinterpret_cast<const cpx<R>*>(d.tw);
 
   cpx<R> vg[E], vy[E];
@@ -1750,8 +1780,9 @@ inline int launch_dual_one(const PassDesc& d, const void* in_y, void* out_y, dou
                            cudaStream_t s) {
   using Sh = DualShape<R, L>;
   const int nlines = COL ? d.Ny : d.Nx;
-  dual_pass_kernel<R, L, COL><<<dual_blocks<R, L>(nlines), Sh::THREADS, Sh::SMEM, s>>>(d, in_y, out_y, partials,
-                                                                                      accumulate);
+  const int nb = d.nbatch > 1 ? d.nbatch : 1;
+  dual_pass_kernel<R, L, COL><<<nb * dual_blocks<R, L>(nlines), Sh::THREADS, Sh::SMEM, s>>>(d, in_y, out_y, partials,
+                                                                                           accumulate);
   return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
 }
 

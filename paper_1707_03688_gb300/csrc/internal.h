@@ -61,7 +61,19 @@ struct PassDesc {
   // a row-major output pass multiplies each stored value by the same element
   // of this caller array (the output's shape and type) when non-null
   const void* post_mask;
+  // same-plan batches: nbatch fields (<= 1: one), field b at in + b * in_bstride
+  // and out + b * out_bstride (elements); the adjoint's value path uses the
+  // same strides
+  int nbatch;
+  long long in_bstride, out_bstride;
 };
+
+// FP32 lines of 256..4096 points run in the line-pair kernel (which also
+// walks a whole same-plan batch in one launch); 0 at build time disables it.
+#ifndef NSLCT_PAIR
+#define NSLCT_PAIR 1
+#endif
+inline bool pair_kernel_length(int L) { return NSLCT_PAIR && L >= 256 && L <= 4096 && (L & (L - 1)) == 0; }
 
 // Enqueue one pass. `col` selects the axis. Returns an NSLCT_* code.
 int launch_pass_f32(bool col, const PassDesc& d, cudaStream_t s);
@@ -115,7 +127,8 @@ struct nslct_plan_s {
   int has_theta;       // A invertible: theta and its chirp Jacobian are defined
   double theta[10];    // (c11,c12,c22, l11,l12,l21,l22, b11,b12,b22), see grad_math.cpp
   double jac[120];     // d(H, B', C1, C2 entries)/d theta, 12 x 10
-  void* ws;            // backward value-path field (made on first use)
+  void* ws;            // backward value-path field(s) (made on first use, grown for batches)
+  long long ws_elems;  // elements `ws` holds
   double* partials;    // backward per-CTA sums (made on first use)
   int partials_stride; // rows per pass in `partials`
   unsigned int* err;   // device status word shared by the plan's kernels

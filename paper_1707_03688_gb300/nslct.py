@@ -44,7 +44,8 @@ NSLCT_PREC_SPLIT_F16 = 0x200
 EXPORTED = (
     "nslct_plan", "nslct_plan_ex", "nslct_derive", "nslct_plan_params", "nslct_plan_info",
     "nslct_plan_padded", "nslct_plan_shape",
-    "nslct_forward", "nslct_forward_masked", "nslct_inverse", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
+    "nslct_forward", "nslct_forward_masked", "nslct_inverse", "nslct_forward_many", "nslct_inverse_many",
+    "nslct_backward_many", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
@@ -96,6 +97,10 @@ def load(path: str | None = None):
         "nslct_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_plan_passes": (ctypes.c_int, [_VP]),
         "nslct_forward_masked": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+        "nslct_forward_many": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
+        "nslct_inverse_many": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
+        "nslct_backward_many": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong, _VP, _VP, _VP, _VP, _VP, _VP,
+                                               _VP]),
         "nslct_forward_pass": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
         "nslct_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "nslct_backward_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -244,6 +249,20 @@ def _check_field(x, nx, ny, dtype, device, name):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _check_batch(x, nx, ny, dtype, device, name):
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and x.device.index != device:
+        raise ValueError(f"{name} is on cuda:{x.device.index}, the plan on cuda:{device}")
+    if x.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {x.dtype}")
+    if tuple(x.shape[1:]) != (nx, ny) or x.shape[0] < 1:
+        raise ValueError(f"{name} must have shape (B, {nx}, {ny}), got {tuple(x.shape)}")
+    if x.stride(2) != 1 or x.stride(1) != ny or (x.shape[0] > 1 and x.stride(0) < nx * ny):
+        raise ValueError(f"{name}: each field must be contiguous and fields must not overlap")
+
+
 def nslct_forward(plan: int, x, out, stream=None):
     """out = L x on `stream` (default: the current torch stream of out's device)."""
     _check(load().nslct_forward(_VP(plan), _VP(x.data_ptr()), _VP(out.data_ptr()), _stream_ptr(stream, out.device)),
@@ -256,6 +275,24 @@ def nslct_forward_masked(plan: int, x, mask, out, stream=None):
     _check(load().nslct_forward_masked(_VP(plan), _VP(x.data_ptr()), _VP(mask.data_ptr()), _VP(out.data_ptr()),
                                        _stream_ptr(stream, out.device)), "nslct_forward_masked")
     return out
+
+
+def nslct_forward_many(plan: int, x, out, stream=None, inverse: bool = False):
+    """The transform (or inverse) of every field of a [B, rows, cols] batch."""
+    fn = load().nslct_inverse_many if inverse else load().nslct_forward_many
+    _check(fn(_VP(plan), int(x.shape[0]), _VP(x.data_ptr()), int(x.stride(0)), _VP(out.data_ptr()),
+              int(out.stride(0)), _stream_ptr(stream, out.device)),
+           "nslct_inverse_many" if inverse else "nslct_forward_many")
+    return out
+
+
+def nslct_backward_many(plan: int, grad_out, y, grad_in, grad_theta=None, grad_chirp=None, workspace=None,
+                        stream=None):
+    """Batched nslct_backward: [B, rows, cols] tensors with one field stride."""
+    _check(load().nslct_backward_many(_VP(plan), int(grad_out.shape[0]), int(grad_out.stride(0)), _ptr(grad_out),
+                                      _ptr(y), _ptr(grad_in), _ptr(grad_theta), _ptr(grad_chirp), _ptr(workspace),
+                                      _stream_ptr(stream, grad_in.device)), "nslct_backward_many")
+    return grad_in
 
 
 def nslct_inverse(plan: int, x, out, stream=None):
@@ -397,18 +434,29 @@ class Plan:
         return nslct_plan_theta_get(self.handle)
 
     def backward(self, grad_out, y, grad_in=None, want_theta=True, want_chirp=False, workspace=None, stream=None):
-        """Returns (grad_in, grad_theta or None, grad_chirp or None); gradients are device float64 tensors."""
+        """Returns (grad_in, grad_theta or None, grad_chirp or None); gradients are device float64 tensors.
+        3D [B, rows, cols] tensors (one field stride for all) give the batch's
+        per-field grad_in and the parameter gradients summed over the batch."""
         import torch
-        _check_field(grad_out, self.nx, self.ny, self.dtype, self.device, "grad_out")
-        _check_field(y, self.nx, self.ny, self.dtype, self.device, "y")
+        batched = grad_out.dim() == 3
+        chk = (lambda t, name: _check_batch(t, self.nx, self.ny, self.dtype, self.device, name)) if batched else \
+            (lambda t, name: _check_field(t, self.nx, self.ny, self.dtype, self.device, name))
+        chk(grad_out, "grad_out")
+        chk(y, "y")
         if grad_in is None:
             grad_in = torch.empty_like(grad_out)
-        _check_field(grad_in, self.nx, self.ny, self.dtype, self.device, "grad_in")
+        chk(grad_in, "grad_in")
         if workspace is not None:
-            _check_field(workspace, self.nx, self.ny, self.dtype, self.device, "workspace")
+            chk(workspace, "workspace")
+        if batched and any(t is not None and (t.shape[0] != grad_out.shape[0] or t.stride(0) != grad_out.stride(0))
+                           for t in (y, grad_in, workspace)):
+            raise ValueError("batched backward arrays must share batch size and field stride")
         gth = torch.zeros(10, dtype=torch.float64, device=grad_out.device) if want_theta else None
         gch = torch.zeros(12, dtype=torch.float64, device=grad_out.device) if want_chirp else None
-        nslct_backward(self.handle, grad_out, y, grad_in, gth, gch, workspace, stream)
+        if batched:
+            nslct_backward_many(self.handle, grad_out, y, grad_in, gth, gch, workspace, stream)
+        else:
+            nslct_backward(self.handle, grad_out, y, grad_in, gth, gch, workspace, stream)
         return grad_in, gth, gch
 
     def passes(self) -> int:
@@ -425,6 +473,15 @@ class Plan:
         (ir, ic), (orr, oc) = nslct_plan_shape(self.handle)
         if inverse:
             (ir, ic), (orr, oc) = (orr, oc), (ir, ic)
+        if x.dim() == 3:
+            # a same-plan batch [B, rows, cols]: fields may be strided along B only
+            _check_batch(x, ir, ic, self.dtype, self.device, "input")
+            if out is None:
+                out = torch.empty((x.shape[0], orr, oc), dtype=x.dtype, device=x.device)
+            _check_batch(out, orr, oc, self.dtype, self.device, "output")
+            if out.shape[0] != x.shape[0]:
+                raise ValueError("input and output batches differ in size")
+            return out
         _check_field(x, ir, ic, self.dtype, self.device, "input")
         if out is None:
             out = torch.empty((orr, oc), dtype=x.dtype, device=x.device)
@@ -432,8 +489,13 @@ class Plan:
         return out
 
     def forward(self, x, out=None, stream=None, mask=None):
-        """L x, or mask * (L x) with the mask fused into the last pass."""
+        """L x, or mask * (L x) with the mask fused into the last pass. A 3D
+        tensor [B, rows, cols] is transformed field by field in batched passes."""
         out = self._prep(x, out)
+        if x.dim() == 3:
+            if mask is not None:
+                raise ValueError("masks apply to single fields")
+            return nslct_forward_many(self.handle, x, out, stream)
         if mask is None:
             return nslct_forward(self.handle, x, out, stream)
         _check_field(mask, out.shape[0], out.shape[1], self.dtype, self.device, "mask")
@@ -441,6 +503,8 @@ class Plan:
 
     def inverse(self, x, out=None, stream=None):
         out = self._prep(x, out, inverse=True)
+        if x.dim() == 3:
+            return nslct_forward_many(self.handle, x, out, stream, inverse=True)
         return nslct_inverse(self.handle, x, out, stream)
 
     def close(self):
