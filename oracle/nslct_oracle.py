@@ -24,7 +24,7 @@ float64/complex128 (no FFT anywhere):
 * ``direct``  -- the sampled continuous kernel ("direct method"), Eq. Intro32.
 * ``project_sp4`` -- nearest-symplectic clean-up of 4-decimal printed matrices.
 
-Readings taken where the paper is silent or ambiguous (all listed in the design doc):
+Readings taken where the paper is silent or ambiguous:
 
 1. Index origin: samples are centred, m = i - floor(N/2) for storage index i;
    the same centred range is used for output and frequency indices.

@@ -149,3 +149,20 @@ def test_backward_rejects_misaligned_and_singular_a(N):
     gx, _, gch = plan.backward(g, g, want_theta=False, want_chirp=True)
     torch.cuda.synchronize()
     assert float(torch.abs(gch).sum()) == 0.0
+
+
+def test_backward_is_deterministic(N):
+    """The CTA partial sums are reduced in a fixed order: repeated calls give
+    bit-identical gradients."""
+    nx = ny = 256
+    m, h0, x, yt = _case(nx, ny, 13)
+    plan = N.Plan(m, nx, ny)
+    xd = torch.from_numpy(x).to(torch.complex64).cuda()
+    y = plan.forward(xd)
+    gy = 2 * (y - torch.from_numpy(yt).to(torch.complex64).cuda())
+    first = plan.backward(gy, y, want_theta=True, want_chirp=True)
+    for _ in range(3):
+        again = plan.backward(gy, y, want_theta=True, want_chirp=True)
+        torch.cuda.synchronize()
+        for a, b in zip(first, again):
+            assert torch.equal(a, b)
