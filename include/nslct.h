@@ -404,6 +404,17 @@ int nslct_batch_destroy(nslct_batch_t batch);
  */
 int nslct_status(nslct_plan_t plan);
 
+/*
+ * nslct_selftest_timeout -- exercise the bounded waits: enqueue the first pass
+ * of `plan`'s forward chain with every panel's barrier expecting 16 bytes more
+ * than its copies bring and a 1 ms limit, so that each CTA's wait expires,
+ * sets the plan's status word and returns (every copy it issued still lands;
+ * nothing faults or hangs). `out` receives no result. Afterwards
+ * nslct_status reports NSLCT_E_TIMEOUT once and the plan works normally.
+ * FP32 plans whose rows are 256..4096 points; in != out, 16-byte aligned.
+ */
+int nslct_selftest_timeout(nslct_plan_t plan, const void* in, void* out, nslct_stream_t stream);
+
 /* nslct_destroy -- free a plan and its device tables (NULL is allowed). */
 int nslct_destroy(nslct_plan_t plan);
 

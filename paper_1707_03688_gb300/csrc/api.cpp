@@ -598,6 +598,22 @@ int nslct_forward_pass(nslct_plan_t p, int pass, const void* in, void* out, nslc
   return run_chain(p, in, out, stream, false, pass, pass);
 }
 
+int nslct_selftest_timeout(nslct_plan_t p, const void* in, void* out, nslct_stream_t stream) {
+  if (!p || !in || !out || in == out) return NSLCT_E_ARG;
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return NSLCT_E_ARG;
+  if (p->prec != 0 || p->mixed || p->padded || !pair_kernel_length(p->Ny)) return NSLCT_E_UNSUPPORTED;
+  DeviceGuard g(p->device);
+  if (!g.ok) return NSLCT_E_CUDA;
+  PassDesc d[5];
+  bool cols[5];
+  build_schedule(p, in, out, false, d, cols);
+  // the first pass, with each panel's barrier armed for 16 bytes more than
+  // its copies bring and a 1 ms limit: every wait expires, every copy lands
+  d[0].test_extra_tx = 16;
+  d[0].wait_us = 1000;
+  return launch(p, cols[0], d[0], reinterpret_cast<cudaStream_t>(stream));
+}
+
 int nslct_status(nslct_plan_t p) {
   if (!p) return NSLCT_E_ARG;
   DeviceGuard g(p->device);

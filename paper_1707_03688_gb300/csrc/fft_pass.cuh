@@ -896,11 +896,23 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// Bounded wait (one thread) for the mbarrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (one thread) for the mbarrier phase with the given parity:
+// false once wait_us microseconds (0: one second) have passed on the global
+// timer. try_wait may suspend the thread for a while on each call, so the
+// bound is on elapsed time, not on the number of calls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned int wait_us) {
+  const uint64_t limit = (uint64_t)(wait_us ? wait_us : 1000000u) * 1000ull;
+  const uint64_t t0 = global_ns();
+  while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (global_ns() - t0 > limit) return false;
+  }
 }
 
 template <int L, bool COL, int E_ = kernel_elems(L, true)> struct PShape {
@@ -1043,14 +1055,14 @@ pass_kernel_tma(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __
     const uint32_t parity = (uint32_t)((it / NIN) & 1);
     float2* buf = stg_in + b * Sh::STG;
     if (tid == 0) {
-      s_ok = mbar_wait_bounded(bar + b, parity) ? 1 : 0;
+      s_ok = mbar_wait_bounded(bar + b, parity, d.wait_us) ? 1 : 0;
       if (COL) bulk_wait_read_all();  // the previous panel's stores have left stg_out
     }
     __syncthreads();
     if (!s_ok) {
       if (tid == 0) {
         if (d.err) atomicOr(d.err, 1u);
-        for (int k = 0; k < NIN; ++k) mbar_wait_bounded(bar + k, (uint32_t)(((it + k) / NIN) & 1));
+        for (int k = 0; k < NIN; ++k) mbar_wait_bounded(bar + k, (uint32_t)(((it + k) / NIN) & 1), d.wait_us);
         bulk_wait_all();
       }
       return;
@@ -1281,16 +1293,16 @@ __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, con
   if (COL) {
     const int rows = d.Nx >> 1;
     const int box = col_box_rows(rows);
-    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * rows * 4 * sizeof(float2)));
+    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * rows * 4 * sizeof(float2)) + d.test_extra_tx);
     for (int g = 0; g < pairs; ++g)
       for (int y0 = 0; y0 < rows; y0 += box)
         tma_load_3d(reinterpret_cast<float2*>(x + g * Sh::LS) + y0 * 4, map, 2 * (first + 2 * g), y0, b, bar);
   } else if (d.in_tiled) {
-    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)));
+    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)) + d.test_extra_tx);
     for (int g = 0; g < pairs; ++g)
       bulk_load(x + g * Sh::LS, in + (size_t)((first >> 1) + g) * (2 * L), 2 * L * sizeof(float2), bar);
   } else if (!d.pad_in) {
-    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)));
+    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)) + d.test_extra_tx);
     for (int g = 0; g < pairs; ++g)
       for (int h = 0; h < 2; ++h)
         bulk_load(reinterpret_cast<float2*>(x + g * Sh::LS) + h * (L + 8), in + (size_t)(first + 2 * g + h) * L,
@@ -1302,7 +1314,7 @@ __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, con
     for (int g = 0; g < pairs; ++g)
       for (int h = 0; h < 2; ++h)
         if ((unsigned)(first + 2 * g + h - d.in_r0) < (unsigned)d.in_rows) bytes += d.in_cols * sizeof(float2);
-    mbar_arrive_expect_tx(bar, bytes);
+    mbar_arrive_expect_tx(bar, bytes + d.test_extra_tx);
     for (int g = 0; g < pairs; ++g)
       for (int h = 0; h < 2; ++h) {
         const int r = first + 2 * g + h - d.in_r0;
@@ -1357,7 +1369,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
     const int first = panel * P;
     const int line0 = first + 2 * g;
     const bool valid = line0 < nlines;          // lines come in pairs (even counts)
-    if (tid == 0) s_ok = mbar_wait_bounded(bar, (uint32_t)(it & 1)) ? 1 : 0;
+    if (tid == 0) s_ok = mbar_wait_bounded(bar, (uint32_t)(it & 1), d.wait_us) ? 1 : 0;
     __syncthreads();
     if (!s_ok) {
       if (tid == 0) {

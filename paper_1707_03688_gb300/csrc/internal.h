@@ -66,6 +66,11 @@ struct PassDesc {
   // same strides
   int nbatch;
   long long in_bstride, out_bstride;
+  // bounded waits: give up after wait_us microseconds (0: one second); a
+  // self-test arms the first panel's barrier for test_extra_tx more bytes than
+  // are copied, so that its wait must expire
+  unsigned int wait_us;
+  unsigned int test_extra_tx;
 };
 
 // FP32 lines of 256..4096 points run in the line-pair kernel (which also

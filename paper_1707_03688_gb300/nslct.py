@@ -50,7 +50,7 @@ EXPORTED = (
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
     "nslct_batch_tune", "nslct_batch_forward_each", "nslct_batch_destroy",
-    "nslct_status", "nslct_destroy", "nslct_strerror", "nslct_version",
+    "nslct_status", "nslct_selftest_timeout", "nslct_destroy", "nslct_strerror", "nslct_version",
 )
 
 
@@ -96,6 +96,7 @@ def load(path: str | None = None):
         "nslct_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_plan_passes": (ctypes.c_int, [_VP]),
+        "nslct_selftest_timeout": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_forward_masked": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
         "nslct_forward_many": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
         "nslct_inverse_many": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
@@ -348,6 +349,12 @@ def nslct_plan_theta_get(plan: int):
 def nslct_status(plan: int) -> int:
     """NSLCT_OK or NSLCT_E_TIMEOUT (a bounded device wait expired since the last call)."""
     return int(load().nslct_status(_VP(plan)))
+
+
+def nslct_selftest_timeout(plan: int, x, out, stream=None):
+    """Run the first pass with waits that must expire (see include/nslct.h)."""
+    _check(load().nslct_selftest_timeout(_VP(plan), _VP(x.data_ptr()), _VP(out.data_ptr()),
+                                         _stream_ptr(stream, out.device)), "nslct_selftest_timeout")
 
 
 def nslct_destroy(plan: int):

@@ -279,3 +279,39 @@ def test_fp64_4096_full_oracle(N, field_4096):
     out = _gpu(plan, field_4096)
     ref = _oracle(plan, field_4096)
     assert O.rel_l2(out, ref) < tol64(4096, 4096)
+
+
+def test_bounded_wait_expires_and_plan_recovers(N):
+    """Failure detection without a fault: a pass whose barriers can never
+    complete gives up after 1 ms in every CTA, the plan's status word reports
+    it once, and the plan (and context) keep working."""
+    n = 256
+    plan = _plan(N, I.random_symplectic_abcd(1), n, n)
+    g = I.blob_field(n, n, seed=1)
+    x = torch.from_numpy(g).to(torch.complex64).cuda()
+    junk = torch.empty_like(x)
+    assert N.nslct_status(plan.handle) == N.NSLCT_OK
+    N.nslct_selftest_timeout(plan.handle, x, junk)
+    torch.cuda.synchronize()
+    assert N.nslct_status(plan.handle) == N.NSLCT_E_TIMEOUT
+    assert N.nslct_status(plan.handle) == N.NSLCT_OK
+    out = _gpu(plan, g)
+    assert N.nslct_status(plan.handle) == N.NSLCT_OK
+    assert O.rel_l2(out, _oracle(plan, g)) < TOL32
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_fractional_fourier_eigenfunctions(N, precision):
+    """The GPU chain keeps Hermite-Gaussians as eigenfunctions of the 2D
+    fractional Fourier case (eigenvalue exp(-j (k + l + 1) phi))."""
+    n, phi = 512, 0.7
+    d = I.default_spacing(n)
+    c, s = math.cos(phi), math.sin(phi)
+    e = np.eye(2)
+    m = np.block([[c * e, s * e], [-s * e, c * e]])
+    plan = _plan(N, m, n, n, precision=precision)
+    for k, l in [(0, 0), (2, 3), (6, 1)]:
+        g = I.hg_field([(k, l)], n, d)
+        out = _gpu(plan, g)
+        lam = np.exp(-1j * (k + l + 1) * phi)
+        assert O.rel_l2(out, lam * g) < (TOL32 if precision == "fp32" else 1e-11), (k, l)

@@ -548,3 +548,21 @@ def test_trace_rule():
         assert O.uses_type2(m) == (tb < 0)
         if tb != 0:
             assert O.uses_type2(O.symplectic_inverse(m)) != O.uses_type2(m)
+
+
+@pytest.mark.parametrize("phi", [0.4, 1.1])
+def test_fractional_fourier_case_has_hermite_gaussian_eigenfunctions(phi):
+    """For M = (cos phi I, sin phi I; -sin phi I, cos phi I) the NsLCT is the 2D
+    fractional Fourier transform, whose eigenfunctions are the Hermite-Gaussians
+    HG_{k,l} (Eq. Acc16) with eigenvalues exp(-j (k + l + 1) phi). Under the
+    sampling condition the chain reproduces both, global phase included."""
+    n = 64
+    d = float(np.sqrt(2 * np.pi / n))
+    c, s = np.cos(phi), np.sin(phi)
+    e = np.eye(2)
+    m = np.block([[c * e, s * e], [-s * e, c * e]])
+    for k, l in [(0, 0), (1, 2), (3, 1), (2, 5)]:
+        g = I.hg_field([(k, l)], n, d)
+        out = O.transform(g, m, d, d)
+        lam = np.exp(-1j * (k + l + 1) * phi)
+        assert np.linalg.norm(out - lam * g) < 1e-12 * np.linalg.norm(g), (k, l)
