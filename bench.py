@@ -45,7 +45,7 @@ BYTES_PER_SAMPLE_PASS = 16        # read + write one complex64 per sample per pa
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per 4096^2 launch of the
 # current FP32 pass kernels (one full capture of one forward transform; row:
 # the mean of passes 1, 3, 5). Reset to None whenever those kernels change.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"pass_kernel_pair<4096,row>": 210.0e6, "pass_kernel_pair<4096,col>": 215.1e6}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
