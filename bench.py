@@ -45,7 +45,7 @@ BYTES_PER_SAMPLE_PASS = 16        # read + write one complex64 per sample per pa
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per 4096^2 launch of the
 # current FP32 pass kernels (one full capture of one forward transform; row:
 # the mean of passes 1, 3, 5). Reset to None whenever those kernels change.
-NCU_TRAFFIC = {"pass_kernel_pair<4096,row>": 210.0e6, "pass_kernel_pair<4096,col>": 215.1e6}
+NCU_TRAFFIC = {}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
@@ -419,7 +419,7 @@ def run_batch_workload(args, world, rank):
         "config": {"workload": "256 fields, Nx and Ny each from {128,...,2048}, own ABCD per field, forward, "
                                "batched persistent launches (autotuned split) captured in one CUDA graph",
                    "samples_per_step": samples, "l2": "working set 2 x samples x 8 B > L2",
-                   "tuned_split": split},
+                   "tuned_split": split, "tuned_cta_threads": b.threads},
         "per_field_launches": {"ms_per_step": ms_each, "value": samples / (ms_each * 1e-3) / 1e6},
         "all_batched_no_graph": {"ms_per_step": ms_all_batched, "value": samples / (ms_all_batched * 1e-3) / 1e6},
         "tuned_no_graph": {"ms_per_step": ms_launch, "value": samples / (ms_launch * 1e-3) / 1e6},

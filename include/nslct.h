@@ -378,10 +378,14 @@ int nslct_batch_capture(nslct_batch_t batch, nslct_stream_t stream);
  */
 int nslct_batch_set_split(nslct_batch_t batch, int split);
 int nslct_batch_get_split(nslct_batch_t batch);
+/* nslct_batch_threads -- the CTA size of the batched kernels: 256 (two CTAs per
+ * SM; the default when every line is at most 2048 points) or 512. */
+int nslct_batch_threads(nslct_batch_t batch);
 
 /*
- * nslct_batch_tune -- autotune the split on the bound buffers: for every
- * distinct shorter side (and "batch everything") run one warm-up forward and
+ * nslct_batch_tune -- autotune the split and the batched kernels' CTA size on
+ * the bound buffers: for every distinct shorter side (and "batch everything"),
+ * and each CTA size that handles every line, run one warm-up forward and
  * `iters` timed forwards on `stream` (CUDA events), keep the fastest, and
  * return it in *chosen (nullable) with its time per forward in
  * *ms_per_forward (nullable). Synchronises `stream`. Overwrites the bound

@@ -231,6 +231,8 @@ int nslct_batch_set_split(nslct_batch_t b, int split) {
 
 int nslct_batch_get_split(nslct_batch_t b) { return b ? b->split : 0; }
 
+int nslct_batch_threads(nslct_batch_t b) { return b ? b->threads : 0; }
+
 int nslct_batch_tune(nslct_batch_t b, nslct_stream_t stream, int iters, int* chosen, float* ms_per_forward) {
   if (!b || !b->bound || iters < 1) return NSLCT_E_ARG;
   for (int f = 0; f < b->n; ++f)
@@ -248,25 +250,37 @@ int nslct_batch_tune(nslct_batch_t b, nslct_stream_t stream, int iters, int* cho
     if (e0) cudaEventDestroy(e0);
     return NSLCT_E_CUDA;
   }
-  int best = 1 << 30, rc = NSLCT_OK;
+  // the batched kernels' CTA size is the other tuned choice: 256 threads (two
+  // CTAs per SM, lines up to 2048) or 512
+  std::vector<int> tile = {512};
+  bool fits256 = true;
+  for (int f = 0; f < b->n && fits256; ++f)
+    fits256 = batch_panel_lines(b->Nx[f], 256) != 0 && batch_panel_lines(b->Ny[f], 256) != 0;
+  if (fits256) tile.push_back(256);
+  int best = 1 << 30, best_th = b->threads, rc = NSLCT_OK;
   float best_ms = 0.0f;
-  for (int c : cands) {
-    b->split = c;
-    rc = build_items(b);
-    if (rc == NSLCT_OK) rc = enqueue(b, s);  // warm-up
-    if (rc == NSLCT_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = NSLCT_E_CUDA;
-    for (int i = 0; rc == NSLCT_OK && i < iters; ++i) rc = enqueue(b, s);
-    if (rc == NSLCT_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
-      rc = NSLCT_E_CUDA;
-    float ms = 0.0f;
-    if (rc == NSLCT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = NSLCT_E_CUDA;
+  for (int th : tile) {
+    for (int c : cands) {
+      b->threads = th;
+      b->split = c;
+      rc = build_items(b);
+      if (rc == NSLCT_OK) rc = enqueue(b, s);  // warm-up
+      if (rc == NSLCT_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = NSLCT_E_CUDA;
+      for (int i = 0; rc == NSLCT_OK && i < iters; ++i) rc = enqueue(b, s);
+      if (rc == NSLCT_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        rc = NSLCT_E_CUDA;
+      float ms = 0.0f;
+      if (rc == NSLCT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = NSLCT_E_CUDA;
+      if (rc != NSLCT_OK) break;
+      ms /= (float)iters;
+      if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = c; best_th = th; }
+    }
     if (rc != NSLCT_OK) break;
-    ms /= (float)iters;
-    if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->split = best;
+  b->threads = best_th;
   const int rc2 = build_items(b);
   if (rc == NSLCT_OK) rc = rc2;
   if (chosen) *chosen = best;

@@ -1137,7 +1137,7 @@ bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P
 // The same as a 3D map over a batch of nbatch fields bstride elements apart
 // (the batch index is the third coordinate).
 bool encode_column_map_batched(CUtensorMap* map, const void* base, int Nx, int Ny, int P, int nbatch,
-                               long long bstride);
+                               long long bstride, int box_rows);
 
 // ---------------------------------------------------------------------------
 // v4 (FP32, power-of-two lines of 256..4096): line-pair kernel.
@@ -1166,6 +1166,20 @@ bool encode_column_map_batched(CUtensorMap* map, const void* base, int Nx, int N
 #ifndef NSLCT_PAIR_COL_TMA_STORE
 #define NSLCT_PAIR_COL_TMA_STORE 1
 #endif
+// column passes with TMA stores: the upper half of each column pair leaves from
+// the landing buffer, the lower half from a separate 32 KB buffer, so the next
+// panel's lower half can be loaded while the stores drain (1), or the whole
+// panel leaves from the landing buffer and the next load waits for it (0)
+#ifndef NSLCT_PAIR_SPLIT_STORE
+#define NSLCT_PAIR_SPLIT_STORE 1
+#endif
+
+// Row pairs per TMA box of a pair-kernel column panel: half the panel or less,
+// so that the two halves load and store separately.
+__host__ __device__ __forceinline__ int pair_box_rows(int rows) {
+  if (!NSLCT_PAIR_SPLIT_STORE) return rows <= 256 ? rows : (rows % 256 == 0 ? 256 : 128);
+  return rows / 2 < 256 ? rows / 2 : 256;
+}
 
 template <int L> struct PairShape {
   static constexpr int E = 16;
@@ -1176,8 +1190,11 @@ template <int L> struct PairShape {
   static constexpr int SH = pad_shift(E);
   static constexpr int LS = L + (L >> SH);        // float4 entries per pair region (padded)
   static constexpr size_t SMEM = (size_t)G * LS * sizeof(float4) + 64;
+  // column passes: the separate output buffer of the lower halves (G L/2 entries)
+  static constexpr int OSTG = NSLCT_PAIR_SPLIT_STORE ? G * (L / 2) : 0;
+  static constexpr size_t SMEM_COL = SMEM + (size_t)OSTG * sizeof(float4);
   static_assert(is_pow2(L) && L >= 256 && L <= 4096, "pair kernel lengths");
-  static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
+  static_assert(SMEM_COL <= 113 * 1024, "two CTAs per SM");
   static_assert((LS * sizeof(float4)) % 128 == 0, "TMA destinations on 128-byte boundaries");
   static_assert(2 * (L + 8) <= 2 * LS, "row landing fits the pair region");
 };
@@ -1284,18 +1301,21 @@ template <int L> struct PairFft {
 // Thread 0: copies of one panel (G line pairs from line `first`) into the
 // pair regions of `x`, arming the mbarrier. Column pairs: one 2D box column
 // (4 complex wide) per pair; row pairs: one or two 1D bulk copies per pair.
+// half (column panels): 0 = the whole panel; 1 = arm the barrier for the
+// whole panel and load the lower row pairs; 2 = load the upper row pairs.
 template <int L, bool COL>
 __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, const CUtensorMap* map,
-                                                const PassDesc& d, int first, uint64_t* bar, int b) {
+                                                const PassDesc& d, int first, uint64_t* bar, int b, int half = 0) {
   using Sh = PairShape<L>;
   const int nlines = COL ? d.Ny : d.Nx;
   const int pairs = min(Sh::G, (nlines - first) >> 1);
   if (COL) {
     const int rows = d.Nx >> 1;
-    const int box = col_box_rows(rows);
-    mbar_arrive_expect_tx(bar, (uint32_t)(pairs * rows * 4 * sizeof(float2)) + d.test_extra_tx);
+    const int box = pair_box_rows(rows);
+    if (half != 2) mbar_arrive_expect_tx(bar, (uint32_t)(pairs * rows * 4 * sizeof(float2)) + d.test_extra_tx);
+    const int r0 = half == 2 ? rows / 2 : 0, r1 = half == 1 ? rows / 2 : rows;
     for (int g = 0; g < pairs; ++g)
-      for (int y0 = 0; y0 < rows; y0 += box)
+      for (int y0 = r0; y0 < r1; y0 += box)
         tma_load_3d(reinterpret_cast<float2*>(x + g * Sh::LS) + y0 * 4, map, 2 * (first + 2 * g), y0, b, bar);
   } else if (d.in_tiled) {
     mbar_arrive_expect_tx(bar, (uint32_t)(pairs * 2 * L * sizeof(float2)) + d.test_extra_tx);
@@ -1335,7 +1355,9 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
   constexpr int P = Sh::P;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float4* xs = reinterpret_cast<float4*>(smem_raw);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(xs + Sh::G * Sh::LS);
+  // the mbarrier after the exchange buffer (and, for column passes, after the
+  // output buffer of the lower halves)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xs + Sh::G * Sh::LS + (COL ? Sh::OSTG : 0));
   volatile int& s_ok = *reinterpret_cast<volatile int*>(bar + 1);
 
   const int tid = threadIdx.x;
@@ -1479,6 +1501,36 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
               make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
         }
       }
+    } else if constexpr (COL && NSLCT_PAIR_SPLIT_STORE) {
+      // lower half (e < L/2) to the separate buffer, upper half stays in place;
+      // the next panel's lower half is loaded while both halves are stored
+      float4* ostg = xs + Sh::G * Sh::LS;
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const int e = t + T * s;
+        const float4 q = make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
+        if (e < L / 2) ostg[g * (L / 2) + e] = q;
+        else xg[e] = q;
+      }
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        const int pairs = min(Sh::G, (nlines - first) >> 1);
+        const int rows = d.Nx >> 1;
+        const int box = pair_box_rows(rows);
+        for (int q = 0; q < pairs; ++q) {
+          for (int y0 = 0; y0 < rows / 2; y0 += box)
+            tma_store_3d(&map_out, 2 * (first + 2 * q), y0, bf, reinterpret_cast<float2*>(ostg + q * (L / 2)) + y0 * 4);
+          for (int y0 = rows / 2; y0 < rows; y0 += box)
+            tma_store_3d(&map_out, 2 * (first + 2 * q), y0, bf, reinterpret_cast<float2*>(xs + q * Sh::LS) + y0 * 4);
+        }
+        bulk_commit();
+        if (next < npanels)
+          pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf, 1);
+        bulk_wait_read_all();  // both output halves have left shared memory
+        if (next < npanels)
+          pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf, 2);
+      }
     } else if constexpr (COL) {
       // leave through the buffer: the box layout is (line0[e], line1[e]) per e
 #pragma unroll
@@ -1489,7 +1541,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       if (tid == 0) {
         const int pairs = min(Sh::G, (nlines - first) >> 1);
         const int rows = d.Nx >> 1;
-        const int box = col_box_rows(rows);
+        const int box = pair_box_rows(rows);
         for (int q = 0; q < pairs; ++q)
           for (int y0 = 0; y0 < rows; y0 += box)
             tma_store_3d(&map_out, 2 * (first + 2 * q), y0, bf, reinterpret_cast<float2*>(xs + q * Sh::LS) + y0 * 4);
@@ -1577,10 +1629,11 @@ inline int launch_one(const PassDesc& d, cudaStream_t s) {
       const int nb = d.nbatch > 1 ? d.nbatch : 1;
       const long long npanels = (long long)((nlines + Sh::P - 1) / Sh::P) * nb;
       const int blocks = npanels < 2 * d.num_sms ? (int)npanels : 2 * d.num_sms;
-      if (COL && (!encode_column_map_batched(&mi, d.in, d.Nx, d.Ny, 2, nb, d.in_bstride) ||
-                  !encode_column_map_batched(&mo, d.out, d.Nx, d.Ny, 2, nb, d.out_bstride)))
+      const int box = pair_box_rows(d.Nx / 2);
+      if (COL && (!encode_column_map_batched(&mi, d.in, d.Nx, d.Ny, 2, nb, d.in_bstride, box) ||
+                  !encode_column_map_batched(&mo, d.out, d.Nx, d.Ny, 2, nb, d.out_bstride, box)))
         return NSLCT_E_CUDA;
-      pass_kernel_pair<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, mi, mo);
+      pass_kernel_pair<L, COL><<<blocks, Sh::THREADS, COL ? Sh::SMEM_COL : Sh::SMEM, s>>>(d, mi, mo);
       return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
     }
     using Sh = PShape<L, COL>;
@@ -1611,7 +1664,7 @@ inline int prepare_one() {
                                   (int)PairShape<L>::SMEM);
       if (e2 == cudaSuccess)
         e2 = cudaFuncSetAttribute(pass_kernel_pair<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)PairShape<L>::SMEM);
+                                  (int)PairShape<L>::SMEM_COL);
     }
     if constexpr (is_pow2(L) && L >= 256) {
       if (e1 == cudaSuccess)

@@ -40,13 +40,14 @@ bool encode_column_map(CUtensorMap* map, const void* base, int Nx, int Ny, int P
 }
 
 bool encode_column_map_batched(CUtensorMap* map, const void* base, int Nx, int Ny, int P, int nbatch,
-                               long long bstride) {
+                               long long bstride, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc || nbatch < 1 || (nbatch > 1 && (bstride < (long long)Nx * Ny || (bstride & 1)))) return false;
   const int rows = Nx / 2;
   const cuuint64_t dims[3] = {(cuuint64_t)(2 * Ny), (cuuint64_t)rows, (cuuint64_t)nbatch};
   const cuuint64_t strides[2] = {(cuuint64_t)(2 * Ny) * 8, (cuuint64_t)(nbatch > 1 ? bstride : (long long)Nx * Ny) * 8};
-  const cuuint32_t box[3] = {(cuuint32_t)(2 * P), (cuuint32_t)(rows <= 256 ? rows : (rows % 256 == 0 ? 256 : 128)), 1};
+  if (box_rows < 1 || box_rows > 256 || rows % box_rows) return false;
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * P), (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,

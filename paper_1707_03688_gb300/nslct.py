@@ -49,6 +49,7 @@ EXPORTED = (
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
+    "nslct_batch_threads",
     "nslct_batch_tune", "nslct_batch_forward_each", "nslct_batch_destroy",
     "nslct_status", "nslct_selftest_timeout", "nslct_destroy", "nslct_strerror", "nslct_version",
 )
@@ -118,6 +119,7 @@ def load(path: str | None = None):
         "nslct_batch_forward_each": (ctypes.c_int, [_VP, _VP]),
         "nslct_batch_set_split": (ctypes.c_int, [_VP, ctypes.c_int]),
         "nslct_batch_get_split": (ctypes.c_int, [_VP]),
+        "nslct_batch_threads": (ctypes.c_int, [_VP]),
         "nslct_batch_tune": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_float)]),
         "nslct_batch_destroy": (ctypes.c_int, [_VP]),
@@ -594,6 +596,11 @@ class Batch:
     @property
     def split(self) -> int:
         return int(load().nslct_batch_get_split(_VP(self.handle)))
+
+    @property
+    def threads(self) -> int:
+        """CTA size of the batched kernels (256 or 512)."""
+        return int(load().nslct_batch_threads(_VP(self.handle)))
 
     def tune(self, stream=None, iters: int = 3):
         """Autotune the split on the bound buffers; returns (split, ms per forward)."""
