@@ -45,7 +45,7 @@ BYTES_PER_SAMPLE_PASS = 16        # read + write one complex64 per sample per pa
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per 4096^2 launch of the
 # current FP32 pass kernels (one full capture of one forward transform; row:
 # the mean of passes 1, 3, 5). Reset to None whenever those kernels change.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"pass_kernel_pair<4096,row>": 209.9e6, "pass_kernel_pair<4096,col>": 215.0e6}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
@@ -79,6 +79,7 @@ class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.05
 
     def __init__(self, device_index: int):
         self.dev = device_index
@@ -92,12 +93,26 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # start timing only once samples are flowing; the samples taken
+            # before that are left out of the summary
+            deadline = time.time() + 5.0
+            while time.time() < deadline and self._lines() == 0:
+                time.sleep(0.02)
+            self.skip = self._lines()
         except Exception:
             self.proc = None
         return self
 
+    def _lines(self) -> int:
+        try:
+            with open(self.path) as f:
+                return sum(1 for ln in f if ln.count(",") >= 8)
+        except OSError:
+            return 0
+
     def __exit__(self, *exc):
         if self.proc is not None:
+            time.sleep(self.PERIOD_S * 1.5)  # the sample that closes the region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -111,7 +126,8 @@ class ClockSampler:
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
-            for line in open(self.path):
+            lines = [ln for ln in open(self.path) if ln.count(",") >= 8][getattr(self, "skip", 0):]
+            for line in lines:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) < 9:
                     continue
@@ -559,7 +575,8 @@ def run_grad_workload(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 50; 10 for --impl reference, whose step takes ~14 s)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -573,6 +590,8 @@ def main():
     ap.add_argument("--n-abcd", type=int, default=16,
                     help="ABCD matrices per step (16 is the benchmark workload; fewer only for profiling captures)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 10 if args.impl == "reference" else 50
     global N_ABCD
     N_ABCD = max(1, min(16, args.n_abcd))
     world, rank, local = _dist_init(args)
