@@ -219,6 +219,19 @@ int nslct_inverse_many(nslct_plan_t plan, int nbatch, const void* in, long long 
                        long long out_stride, nslct_stream_t stream);
 
 /*
+ * nslct_forward_group -- out[k] = L_k in[k] for n independent transforms
+ * (plans on one device; any sizes and flags), enqueued alternately on
+ * `stream` and on a library-owned side stream that forks from and joins back
+ * to `stream`: each transform's passes fill the last partial wave and the
+ * start-up of the other stream's, and everything is complete in `stream`
+ * order when the call's work there completes. Buffer rules as nslct_forward
+ * for each k; the pairs must not overlap one another. Concurrent calls on one
+ * device share the side stream (serialising their side halves). Capturable.
+ */
+int nslct_forward_group(int n, const nslct_plan_t* plans, const void* const* in, void* const* out,
+                        nslct_stream_t stream);
+
+/*
  * nslct_forward_masked -- out = mask .* (L in): the forward transform followed
  * by a pointwise filter in the NsLCT domain (the H1, H3 of Eqs. Add04/Add08),
  * multiplied in the last pass before the store, so it costs one read of the

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -586,6 +587,48 @@ int nslct_inverse_many(nslct_plan_t p, int nbatch, const void* in, long long in_
   const int rc = check_many(p, nbatch, in, in_stride, out, out_stride);
   if (rc != NSLCT_OK) return rc;
   return run_chain(p, in, out, stream, true, 0, nslct_plan_passes(p) - 1, nullptr, nbatch, in_stride, out_stride);
+}
+
+// One side stream and a pair of fork/join events per device, made on first
+// use, for nslct_forward_group.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static std::mutex g_side_mu;
+static SideStream g_side[64];
+
+int nslct_forward_group(int n, const nslct_plan_t* plans, const void* const* in, void* const* out,
+                        nslct_stream_t stream) {
+  if (n < 1 || !plans || !in || !out) return NSLCT_E_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!plans[k] || !in[k] || !out[k] || plans[k]->device != plans[0]->device) return NSLCT_E_ARG;
+  const int dev = plans[0]->device;
+  if (dev < 0 || dev >= 64) return NSLCT_E_ARG;
+  DeviceGuard g(dev);
+  if (!g.ok) return NSLCT_E_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 1) return nslct_forward(plans[0], in[0], out[0], stream);
+  SideStream* ss = &g_side[dev];
+  {
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    if (!ss->s) {
+      if (cudaStreamCreateWithFlags(&ss->s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming) != cudaSuccess)
+        return NSLCT_E_CUDA;
+    }
+  }
+  // transforms 0, 2, 4, ... on the caller's stream, 1, 3, ... on the side
+  // stream, forked from and joined back to the caller's stream
+  if (cudaEventRecord(ss->fork, s) != cudaSuccess || cudaStreamWaitEvent(ss->s, ss->fork, 0) != cudaSuccess)
+    return NSLCT_E_CUDA;
+  int rc = NSLCT_OK;
+  for (int k = 0; k < n && rc == NSLCT_OK; ++k)
+    rc = nslct_forward(plans[k], in[k], out[k], k % 2 == 0 ? stream : reinterpret_cast<nslct_stream_t>(ss->s));
+  if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(s, ss->join, 0) != cudaSuccess)
+    return NSLCT_E_CUDA;
+  return rc;
 }
 
 int nslct_forward_masked(nslct_plan_t p, const void* in, const void* mask, void* out, nslct_stream_t stream) {

@@ -44,7 +44,8 @@ NSLCT_PREC_SPLIT_F16 = 0x200
 EXPORTED = (
     "nslct_plan", "nslct_plan_ex", "nslct_derive", "nslct_plan_params", "nslct_plan_info",
     "nslct_plan_padded", "nslct_plan_shape",
-    "nslct_forward", "nslct_forward_masked", "nslct_inverse", "nslct_forward_many", "nslct_inverse_many",
+    "nslct_forward", "nslct_forward_masked", "nslct_forward_group", "nslct_inverse", "nslct_forward_many",
+    "nslct_inverse_many",
     "nslct_backward_many", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
@@ -99,6 +100,8 @@ def load(path: str | None = None):
         "nslct_plan_passes": (ctypes.c_int, [_VP]),
         "nslct_selftest_timeout": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
         "nslct_forward_masked": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+        "nslct_forward_group": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                               ctypes.POINTER(_VP), _VP]),
         "nslct_forward_many": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
         "nslct_inverse_many": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
         "nslct_backward_many": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -278,6 +281,16 @@ def nslct_forward_masked(plan: int, x, mask, out, stream=None):
     _check(load().nslct_forward_masked(_VP(plan), _VP(x.data_ptr()), _VP(mask.data_ptr()), _VP(out.data_ptr()),
                                        _stream_ptr(stream, out.device)), "nslct_forward_masked")
     return out
+
+
+def nslct_forward_group(plans, xs, outs, stream=None):
+    """out[k] = L_k x[k] for independent transforms, alternated over two streams."""
+    n = len(plans)
+    ph = (_VP * n)(*[_VP(p) for p in plans])
+    pi = (_VP * n)(*[_VP(x.data_ptr()) for x in xs])
+    po = (_VP * n)(*[_VP(o.data_ptr()) for o in outs])
+    _check(load().nslct_forward_group(n, ph, pi, po, _stream_ptr(stream, outs[0].device)), "nslct_forward_group")
+    return outs
 
 
 def nslct_forward_many(plan: int, x, out, stream=None, inverse: bool = False):
