@@ -227,6 +227,8 @@ int nslct_inverse_many(nslct_plan_t plan, int nbatch, const void* in, long long 
  * order when the call's work there completes. Buffer rules as nslct_forward
  * for each k; the pairs must not overlap one another. Concurrent calls on one
  * device share the side stream (serialising their side halves). Capturable.
+ * The side stream is made on the first call per device and kept for the
+ * life of the process (it does not survive cudaDeviceReset).
  */
 int nslct_forward_group(int n, const nslct_plan_t* plans, const void* const* in, void* const* out,
                         nslct_stream_t stream);

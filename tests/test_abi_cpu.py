@@ -152,3 +152,39 @@ def test_derive_type2_is_type1_of_the_inverse(lib):
         dt = N.nslct_derive(m, flags=N.NSLCT_TYPE_BY_TRACE)
         ref = d2 if O.uses_type2(m) else N.nslct_derive(m)
         np.testing.assert_allclose(dt["H"], ref["H"], atol=0)
+
+
+def test_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    """Argument checks that come before any device work."""
+    import ctypes
+    vp = ctypes.c_void_p
+    m = I.random_symplectic_abcd(2)
+    mm, pm = N._dbl(m, 16)
+    h = vp(0)
+    # zero padding: odd field sizes, fields larger than the grid, H given by the caller
+    for args in ((101, 100, 128, 128), (100, 100, 64, 128), (0, 100, 128, 128)):
+        assert lib.nslct_plan_padded(ctypes.byref(h), pm, *args, 0.3, 0.3, ctypes.c_uint(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_plan_padded(ctypes.byref(h), pm, 100, 100, 128, 128, 0.3, 0.3,
+                                 ctypes.c_uint(N.NSLCT_H_USER)) == N.NSLCT_E_ARG
+    assert lib.nslct_plan_padded(ctypes.byref(h), pm, 100, 100, 128, 128, 0.3, 0.3,
+                                 ctypes.c_uint(N.NSLCT_TYPE2)) == N.NSLCT_E_UNSUPPORTED
+    # null plans and empty groups
+    assert lib.nslct_forward_many(vp(0), 2, vp(0), 0, vp(0), 0, vp(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_backward_many(vp(0), 2, 0, vp(0), vp(0), vp(0), vp(0), vp(0), vp(0), vp(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_forward_group(0, None, None, None, vp(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_selftest_timeout(vp(0), vp(0), vp(0), vp(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_plan_shape(vp(0), None, None, None, None) == N.NSLCT_E_ARG
+    assert lib.nslct_plan_passes(vp(0)) == 0
+    assert lib.nslct_batch_tune(vp(0), vp(0), 1, None, None) == N.NSLCT_E_ARG
+    assert lib.nslct_batch_set_split(vp(0), 4) == N.NSLCT_E_ARG
+    assert lib.nslct_batch_threads(vp(0)) == 0
+    # batches: an unsupported size is refused before any plan is made
+    nx = (ctypes.c_int * 1)(100)
+    ny = (ctypes.c_int * 1)(128)
+    dd = (ctypes.c_double * 1)(0.3)
+    b = vp(0)
+    assert lib.nslct_plan_batch(ctypes.byref(b), 1, pm, nx, ny, dd, dd, ctypes.c_uint(0)) == N.NSLCT_E_SIZE
+    assert lib.nslct_plan_batch(ctypes.byref(b), 1, pm, ny, ny, dd, dd,
+                                ctypes.c_uint(N.NSLCT_TYPE2)) == N.NSLCT_E_UNSUPPORTED
+    assert lib.nslct_plan_theta(ctypes.byref(h), (ctypes.c_double * 10)(*([0.1] * 10)), None, 64, 64, 0.3, 0.3,
+                                ctypes.c_uint(N.NSLCT_TYPE2)) == N.NSLCT_E_UNSUPPORTED
