@@ -43,9 +43,21 @@ NOISE_SEED = 102
 ABCD_SEED0 = 200
 BYTES_PER_SAMPLE_PASS = 16        # read + write one complex64 per sample per pass
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per 4096^2 launch of the
-# current FP32 pass kernels (one full capture of one forward transform; row:
-# the mean of passes 1, 3, 5). Reset to None whenever those kernels change.
-NCU_TRAFFIC = {"pass_kernel_pair<4096,row>": 209.9e6, "pass_kernel_pair<4096,col>": 215.0e6}
+# current FP32 pass kernels (one full capture of one forward transform; the
+# column kernel: the mean of passes 2 and 4). Reset whenever a kernel changes.
+NCU_TRAFFIC = {"pass_kernel_pair<4096, 0, 1>": 214.2e6, "pass_kernel_pair<4096, 1, 4>": 215.1e6,
+               "pass_kernel_pair<4096, 0, 2>": 208.1e6, "pass_kernel_pair<4096, 0, 3>": 207.9e6}
+# the kernel (as ncu names it) that runs each pass of the forward transform:
+# the line-pair kernel's template arguments are (length, column pass, mode),
+# the mode naming the first and last transform directions of the pass
+PASS_KERNELS = {
+    ("fp32", 5): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 2>",
+                  "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
+    ("fp32", 3): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
+    ("mixed", 5): ["pass_kernel_tma<4096, 0, 1>", "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>",
+                   "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>"],
+    ("mixed", 3): ["pass_kernel_tma<4096, 0, 1>", "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>"],
+}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
@@ -286,17 +298,16 @@ def run_gpu(args, world, rank, local):
     pass_ms /= len(evs)
     peak, peak_kind = _peaks()
     bytes_launch = BYTES_PER_SAMPLE_PASS * NX * NY
-    # the dominant kernel: of the row-pass and column-pass kernels (passes 1, 3
-    # of five or 1 of three are column passes), the one with the larger share
-    # of the transform's time; its roofline uses its average launch
-    col_idx = [1, 3] if npass == 5 else [1]
-    row_idx = [j for j in range(npass) if j not in col_idx]
-    col_total, row_total = float(np.sum(pass_ms[col_idx])), float(np.sum(pass_ms[row_idx]))
-    kname = "pass_kernel_pair<4096,{}>" if args.precision == "fp32" else "pass_kernel_tma<4096,{},mixed>"
-    if col_total >= row_total:
-        dom_ms, dom_name, dom_share = col_total / len(col_idx), kname.format("col"), col_total / pass_ms.sum()
-    else:
-        dom_ms, dom_name, dom_share = row_total / len(row_idx), kname.format("row"), row_total / pass_ms.sum()
+    # the dominant kernel: of the kernels that run the passes, the one with the
+    # largest share of the transform's time; its roofline uses its average launch
+    names = PASS_KERNELS[(args.precision, npass)]
+    per_kernel = {}
+    for j, name in enumerate(names):
+        tot, n = per_kernel.get(name, (0.0, 0))
+        per_kernel[name] = (tot + float(pass_ms[j]), n + 1)
+    dom_name = max(per_kernel, key=lambda k: per_kernel[k][0])
+    dom_ms = per_kernel[dom_name][0] / per_kernel[dom_name][1]
+    dom_share = per_kernel[dom_name][0] / float(pass_ms.sum())
     achieved = bytes_launch / (dom_ms * 1e-3) / 1e9
     chain_gbs = npass * bytes_launch / (pass_ms.sum() * 1e-3) / 1e9
 

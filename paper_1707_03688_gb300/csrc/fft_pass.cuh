@@ -22,6 +22,7 @@
 
 #include "internal.h"
 #include "fft_schedule.h"
+#include "pair_x2.cuh"
 
 namespace nslct {
 
@@ -1298,6 +1299,148 @@ template <int L> struct PairFft {
   }
 };
 
+// packed line-pair FFT: twiddle powers as scalars broadcast to both lanes (1)
+// or computed in packed form (0)
+#ifndef NSLCT_X2_SCALAR_POWERS
+#define NSLCT_X2_SCALAR_POWERS 1
+#endif
+// The line-pair FFT on packed pairs (pair_x2.cuh): the stages of PairFft with
+// each butterfly and twiddle product done once for both lines. Entry e of a
+// pair region is (re pair, im pair), 16 bytes as in PairFft. Always the
+// forward DFT; an inverse is this code on data held in the J domain.
+template <int L> struct X2Fft {
+  using Sh = PairShape<L>;
+  static constexpr int E = Sh::E;
+  static constexpr int T = Sh::T;
+  static constexpr int S = num_stages(L, E);
+  static constexpr int SH = Sh::SH;
+
+  static __device__ __forceinline__ int sidx(int g, int e) { return g * Sh::LS + padded_by<SH>(e); }
+
+  template <int ST>
+  static __device__ __forceinline__ void stage(cx2* v, ulonglong2* sm, int t, int g, const float2* __restrict__ tw,
+                                               const X2Const& K) {
+    constexpr int RD = stage_radix(L, E, ST);
+    constexpr int NS = stage_ns(L, E, ST);
+    constexpr bool FIRST = (ST == 0);
+    constexpr bool LAST = (ST == S - 1);
+    constexpr int NB = E / RD;
+    static_assert(E % RD == 0, "radix must divide E");
+    if constexpr (!FIRST) {
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const ulonglong2 q = sm[sidx(g, t + T * s)];
+        v[s] = cx2{q.x, q.y};
+      }
+      if constexpr (!LAST) __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      cx2 x[RD];
+#pragma unroll
+      for (int r = 0; r < RD; ++r) x[r] = v[u + r * NB];
+      const int j = t + u * T;
+      const int jm = j % NS;
+      if constexpr (NS > 1) {
+        const float2 wb = __ldg(tw + compact_table_offset(L, E, ST) + jm);
+        if constexpr (NSLCT_X2_SCALAR_POWERS) x2_twiddle_scalar_powers<RD>(x, wb);
+        else x2_twiddle<RD>(x, wb, K);
+      }
+      X2Dft<RD>::run(x, K);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < RD; ++r) v[u + r * NB] = x[r];
+      } else {
+        const int base = (j / NS) * NS * RD + jm;
+#pragma unroll
+        for (int r = 0; r < RD; ++r) sm[sidx(g, base + r * NS)] = make_ulonglong2(x[r].re, x[r].im);
+      }
+    }
+  }
+
+  template <int ST>
+  static __device__ __forceinline__ void stages(cx2* v, ulonglong2* sm, int t, int g, const float2* __restrict__ tw,
+                                                const X2Const& K) {
+    if constexpr (ST < S) {
+      stage<ST>(v, sm, t, g, tw, K);
+      stages<ST + 1>(v, sm, t, g, tw, K);
+    }
+  }
+
+  static __device__ __forceinline__ void run(cx2* v, ulonglong2* sm, int t, int g, const float2* __restrict__ tw) {
+    const X2Const K;
+    __syncthreads();  // the previous user of `sm` is done
+    stages<0>(v, sm, t, g, tw, K);
+  }
+};
+
+// One step of a packed pass program on the thread's E positions of lines
+// line0 and line0 + 1: multiply by the chirp (its phases exactly as in
+// apply_chirp_c, one Q0.64 phase per line) times scale, or by scale alone.
+// conj: the data is held in the J domain, so the chirp is conjugated. SWAP:
+// the results go to the other parts (the step also switches domain); a swap
+// with no step is a multiply by one.
+template <int L, bool COL, bool SWAP>
+__device__ __forceinline__ void x2_step(cx2* v, const X2Step& st, bool conj, const PassDesc& d, int t, int line0) {
+  constexpr int E = PairShape<L>::E;
+  constexpr int T = L / E;
+  if (st.kind == 1) {
+    const int nl = COL ? d.Ny : d.Nx;  // length of the other axis
+    const uint64_t ka = COL ? st.c.k11 : st.c.k22;
+    const uint64_t kb = COL ? st.c.k22 : st.c.k11;
+    const long long a0 = st.freq ? (long long)t : (long long)t - L / 2;
+    const uint64_t dd = 2ull * ka * (uint64_t)((long long)T * T);
+    uint64_t q[2], dq[2], kab[2], base[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long b = st.freq ? (long long)centred_bin(line0 + h, nl) : (long long)(line0 + h) - nl / 2;
+      kab[h] = st.c.k12 * (uint64_t)b;
+      base[h] = kb * (uint64_t)(b * b);
+      q[h] = ka * (uint64_t)(a0 * a0) + kab[h] * (uint64_t)a0 + base[h];
+      dq[h] = ka * (uint64_t)(2 * a0 * T + (long long)T * T) + kab[h] * (uint64_t)T;
+    }
+    const float sc = st.scale, ssc = conj ? -st.scale : st.scale;
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      if (s == E / 2 && st.freq) {
+        // centred bins: the second half of the line holds the negative bins
+        const long long a = a0 + (long long)T * s - L;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          q[h] = ka * (uint64_t)(a * a) + kab[h] * (uint64_t)a + base[h];
+          dq[h] = ka * (uint64_t)(2 * a * T + (long long)T * T) + kab[h] * (uint64_t)T;
+        }
+      }
+      float sn[2], cs[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        // top 32 bits as a signed fraction of a turn in [-1/2, 1/2)
+        const float tt = (float)(int)(unsigned)(q[h] >> 32) * 2.3283064365386963e-10f;  // 2^-32
+        __sincosf(6.28318530717958647692f * tt, &sn[h], &cs[h]);
+        q[h] += dq[h];
+        dq[h] += dd;
+      }
+      // scaled (and for conj negated) sine per line; its negation by an integer XOR
+      const float s0 = sn[0] * ssc, s1 = sn[1] * ssc;
+      const f32x2 cc = x2_pack(cs[0] * sc, cs[1] * sc);
+      const f32x2 ss = x2_pack(s0, s1);
+      const f32x2 nss = x2_pack(__int_as_float(__float_as_int(s0) ^ 0x80000000),
+                                __int_as_float(__float_as_int(s1) ^ 0x80000000));
+      const f32x2 re = x2_fma(v[s].re, cc, x2_mul(v[s].im, nss));
+      const f32x2 im = x2_fma(v[s].re, ss, x2_mul(v[s].im, cc));
+      v[s] = SWAP ? cx2{im, re} : cx2{re, im};
+    }
+  } else if (SWAP || st.kind == 2) {
+    const f32x2 sc = x2_bcast(st.kind == 2 ? st.scale : 1.0f);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const f32x2 re = x2_mul(v[s].re, sc), im = x2_mul(v[s].im, sc);
+      v[s] = SWAP ? cx2{im, re} : cx2{re, im};
+    }
+  }
+}
+
 // Thread 0: copies of one panel (G line pairs from line `first`) into the
 // pair regions of `x`, arming the mbarrier. Column pairs: one 2D box column
 // (4 complex wide) per pair; row pairs: one or two 1D bulk copies per pair.
@@ -1345,7 +1488,11 @@ __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, con
   }
 }
 
-template <int L, bool COL>
+// MODE 0: scalar arithmetic, any sequence of transforms. MODE 1..4: packed
+// FP32x2 (pair_x2.cuh) running the pass program d.x2, whose first and last
+// transforms are (1) forward, forward, (2) inverse, forward, (3) inverse,
+// inverse, (4) forward, inverse.
+template <int L, bool COL, int MODE = 0>
 __global__ void __launch_bounds__(256, 2)
 pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out) {
   using Sh = PairShape<L>;
@@ -1450,30 +1597,64 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       }
     }
 
-    const float scale = d.fscale;
-    if (d.t1 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t1 == kInv);
-    if (d.has_chirp) {
-      apply_chirp_c<float, L, COL, E>(v0, d, d.chirp, d.freq_domain, t, line0, scale);
-      apply_chirp_c<float, L, COL, E>(v1, d, d.chirp, d.freq_domain, t, line0 + 1, scale);
-    } else if (d.scale_only) {
+    if constexpr (MODE == 0) {
+      const float scale = d.fscale;
+      if (d.t1 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t1 == kInv);
+      if (d.has_chirp) {
+        apply_chirp_c<float, L, COL, E>(v0, d, d.chirp, d.freq_domain, t, line0, scale);
+        apply_chirp_c<float, L, COL, E>(v1, d, d.chirp, d.freq_domain, t, line0 + 1, scale);
+      } else if (d.scale_only) {
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          v0[s] = make_float2(v0[s].x * scale, v0[s].y * scale);
+          v1[s] = make_float2(v1[s].x * scale, v1[s].y * scale);
+        }
+      }
+      if (d.t2 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t2 == kInv);
+      if (d.has_chirp2) {
+        apply_chirp_c<float, L, COL, E>(v0, d, d.chirp2, d.freq_domain2, t, line0, d.fscale2);
+        apply_chirp_c<float, L, COL, E>(v1, d, d.chirp2, d.freq_domain2, t, line0 + 1, d.fscale2);
+      } else if (d.fscale2 != 1.0f) {
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          v0[s] = make_float2(v0[s].x * d.fscale2, v0[s].y * d.fscale2);
+          v1[s] = make_float2(v1[s].x * d.fscale2, v1[s].y * d.fscale2);
+        }
+      }
+      if (d.t3 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t3 == kInv);
+    } else {
+      // packed pass program: load in the domain of the first transform (J
+      // for an inverse: the parts swapped), one forward-FFT body for every
+      // transform, each gap's step switching domain, store from the domain
+      // of the last transform
+      constexpr bool FINV = MODE == 2 || MODE == 3;
+      constexpr bool LINV = MODE == 3 || MODE == 4;
+      cx2 v[E];
 #pragma unroll
       for (int s = 0; s < E; ++s) {
-        v0[s] = make_float2(v0[s].x * scale, v0[s].y * scale);
-        v1[s] = make_float2(v1[s].x * scale, v1[s].y * scale);
+        const f32x2 re = x2_pack(v0[s].x, v1[s].x), im = x2_pack(v0[s].y, v1[s].y);
+        v[s] = FINV ? cx2{im, re} : cx2{re, im};
       }
-    }
-    if (d.t2 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t2 == kInv);
-    if (d.has_chirp2) {
-      apply_chirp_c<float, L, COL, E>(v0, d, d.chirp2, d.freq_domain2, t, line0, d.fscale2);
-      apply_chirp_c<float, L, COL, E>(v1, d, d.chirp2, d.freq_domain2, t, line0 + 1, d.fscale2);
-    } else if (d.fscale2 != 1.0f) {
+      if (d.x2.pre.kind) x2_step<L, COL, false>(v, d.x2.pre, FINV, d, t, line0);
+      ulonglong2* xs2 = reinterpret_cast<ulonglong2*>(xs);
+#pragma unroll 1
+      for (int k = 0; k < d.x2.ntr; ++k) {
+        if (k > 0) {
+          // the gap after transform k-1, whose domain is J when it was an inverse
+          const X2Step st = k == 1 ? d.x2.gap[0] : d.x2.gap[1];
+          x2_step<L, COL, true>(v, st, FINV != (((k - 1) & 1) != 0), d, t, line0);
+        }
+        X2Fft<L>::run(v, xs2, t, g, tw);
+      }
+      if (d.x2.post[0].kind) x2_step<L, COL, false>(v, d.x2.post[0], LINV, d, t, line0);
+      if (d.x2.post[1].kind) x2_step<L, COL, false>(v, d.x2.post[1], LINV, d, t, line0);
 #pragma unroll
       for (int s = 0; s < E; ++s) {
-        v0[s] = make_float2(v0[s].x * d.fscale2, v0[s].y * d.fscale2);
-        v1[s] = make_float2(v1[s].x * d.fscale2, v1[s].y * d.fscale2);
+        const cx2 w = LINV ? cx2{v[s].im, v[s].re} : v[s];
+        x2_unpack(w.re, v0[s].x, v1[s].x);
+        x2_unpack(w.im, v0[s].y, v1[s].y);
       }
     }
-    if (d.t3 != kNone) Fft::run(v0, v1, xs, t, g, tw, d.t3 == kInv);
     if (!COL && !d.out_tiled && d.post_mask) {
 #pragma unroll
       for (int s = 0; s < E; ++s) {
@@ -1607,6 +1788,60 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
 }
 
 
+// Pass program of the packed line-pair kernel from the generic descriptor
+// fields: the sequence t1, step 1, t2, step 2, t3 with absent parts skipped
+// (step 1 is the chirp or the lone scale, step 2 chirp2 or fscale2). Returns
+// the kernel mode 1..4 (see pass_kernel_pair) or 0 when the transforms do not
+// alternate in direction, two steps share a gap, or there is no transform.
+inline int x2_program(const PassDesc& d, X2Prog& pg) {
+  X2Step st[2] = {};
+  if (d.has_chirp) st[0] = X2Step{1, d.freq_domain, d.fscale, d.chirp};
+  else if (d.scale_only) st[0] = X2Step{2, 0, d.fscale, Chirp{}};
+  if (d.has_chirp2) st[1] = X2Step{1, d.freq_domain2, d.fscale2, d.chirp2};
+  else if (d.fscale2 != 1.0f) st[1] = X2Step{2, 0, d.fscale2, Chirp{}};
+  const int tr[3] = {d.t1, d.t2, d.t3};
+  pg = X2Prog{};
+  int dirs[3] = {}, n = 0, npend = 0;
+  X2Step pend[2] = {};
+  for (int k = 0; k < 3; ++k) {
+    if (tr[k] != kNone) {
+      if (npend > 1) return 0;
+      if (n == 0) {
+        if (npend) pg.pre = pend[0];
+      } else {
+        pg.gap[n - 1] = npend ? pend[0] : X2Step{};
+      }
+      dirs[n++] = tr[k];
+      npend = 0;
+    }
+    if (k < 2 && st[k].kind) pend[npend++] = st[k];
+  }
+  if (n == 0) return 0;
+  for (int i = 1; i < n; ++i)
+    if (dirs[i] == dirs[i - 1]) return 0;
+  for (int i = 0; i < npend; ++i) pg.post[i] = pend[i];
+  pg.ntr = n;
+  const bool fi = dirs[0] == kInv, li = dirs[n - 1] == kInv;
+  return !fi && !li ? 1 : fi && !li ? 2 : fi && li ? 3 : 4;
+}
+
+// packed line-pair kernel modes built: rows (1) F..F, (2) I..F, (3) I..I;
+// columns (4) F..I; 0 builds the scalar kernel instead
+#ifndef NSLCT_PAIR_X2
+#define NSLCT_PAIR_X2 1
+#endif
+template <bool COL>
+inline bool pair_mode_built(int mode) {
+  if (!NSLCT_PAIR_X2) return mode == 0;
+  return COL ? mode == 4 : (mode >= 1 && mode <= 3);
+}
+
+template <int L, bool COL, int MODE>
+inline void launch_pair(const PassDesc& d, const CUtensorMap& mi, const CUtensorMap& mo, int blocks, cudaStream_t s) {
+  using Sh = PairShape<L>;
+  pass_kernel_pair<L, COL, MODE><<<blocks, Sh::THREADS, COL ? Sh::SMEM_COL : Sh::SMEM, s>>>(d, mi, mo);
+}
+
 template <typename R, int L, bool COL>
 inline int launch_one(const PassDesc& d, cudaStream_t s) {
   const int nlines = COL ? d.Ny : d.Nx;
@@ -1624,30 +1859,62 @@ inline int launch_one(const PassDesc& d, cudaStream_t s) {
         return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
       }
     }
+    using ShT = PShape<L, COL>;
+    // the general FP32 kernel, one field
+    auto launch_tma = [&](const PassDesc& e) -> int {
+      const int npanels = (nlines + ShT::P - 1) / ShT::P;
+      const int blocks = npanels < e.num_sms ? npanels : e.num_sms;
+      if (COL && (!encode_column_map(&mi, e.in, e.Nx, e.Ny, ShT::P) ||
+                  !encode_column_map(&mo, e.out, e.Nx, e.Ny, ShT::P)))
+        return NSLCT_E_CUDA;
+      pass_kernel_tma<L, COL><<<blocks, ShT::THREADS, ShT::SMEM, s>>>(e, mi, mo);
+      return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+    };
     if constexpr (NSLCT_PAIR && is_pow2(L) && L >= 256) {
       using Sh = PairShape<L>;
       const int nb = d.nbatch > 1 ? d.nbatch : 1;
-      const long long npanels = (long long)((nlines + Sh::P - 1) / Sh::P) * nb;
-      const int blocks = npanels < 2 * d.num_sms ? (int)npanels : 2 * d.num_sms;
-      const int box = pair_box_rows(d.Nx / 2);
-      if (COL && (!encode_column_map_batched(&mi, d.in, d.Nx, d.Ny, 2, nb, d.in_bstride, box) ||
-                  !encode_column_map_batched(&mo, d.out, d.Nx, d.Ny, 2, nb, d.out_bstride, box)))
-        return NSLCT_E_CUDA;
-      pass_kernel_pair<L, COL><<<blocks, Sh::THREADS, COL ? Sh::SMEM_COL : Sh::SMEM, s>>>(d, mi, mo);
-      return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+      PassDesc dx = d;
+      const int mode = NSLCT_PAIR_X2 ? x2_program(d, dx.x2) : 0;
+      if (pair_mode_built<COL>(mode)) {
+        const long long npanels = (long long)((nlines + Sh::P - 1) / Sh::P) * nb;
+        const int blocks = npanels < 2 * d.num_sms ? (int)npanels : 2 * d.num_sms;
+        const int box = pair_box_rows(d.Nx / 2);
+        if (COL && (!encode_column_map_batched(&mi, d.in, d.Nx, d.Ny, 2, nb, d.in_bstride, box) ||
+                    !encode_column_map_batched(&mo, d.out, d.Nx, d.Ny, 2, nb, d.out_bstride, box)))
+          return NSLCT_E_CUDA;
+        if constexpr (!NSLCT_PAIR_X2) launch_pair<L, COL, 0>(dx, mi, mo, blocks, s);
+        else if constexpr (COL) launch_pair<L, true, 4>(dx, mi, mo, blocks, s);
+        else if (mode == 1) launch_pair<L, false, 1>(dx, mi, mo, blocks, s);
+        else if (mode == 2) launch_pair<L, false, 2>(dx, mi, mo, blocks, s);
+        else launch_pair<L, false, 3>(dx, mi, mo, blocks, s);
+        return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+      }
+      // a pass program the packed kernel is not built for: the general
+      // kernel, one launch per field of the batch
+      for (int b = 0; b < nb; ++b) {
+        PassDesc e = d;
+        e.nbatch = 1;
+        e.in = static_cast<const float2*>(d.in) + b * d.in_bstride;
+        e.out = static_cast<float2*>(d.out) + b * d.out_bstride;
+        const int rc = launch_tma(e);
+        if (rc != NSLCT_OK) return rc;
+      }
+      return NSLCT_OK;
     }
-    using Sh = PShape<L, COL>;
-    const int npanels = (nlines + Sh::P - 1) / Sh::P;
-    const int blocks = npanels < d.num_sms ? npanels : d.num_sms;
-    if (COL && (!encode_column_map(&mi, d.in, d.Nx, d.Ny, Sh::P) || !encode_column_map(&mo, d.out, d.Nx, d.Ny, Sh::P)))
-      return NSLCT_E_CUDA;
-    pass_kernel_tma<L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, mi, mo);
+    return launch_tma(d);
   } else {
     using Sh = PassShape<R, L>;
     const int blocks = (nlines + Sh::P - 1) / Sh::P;
     pass_kernel<R, L, COL><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d);
   }
   return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
+}
+
+template <int L, bool COL, int MODE>
+inline cudaError_t prepare_pair() {
+  using Sh = PairShape<L>;
+  return cudaFuncSetAttribute(pass_kernel_pair<L, COL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(COL ? Sh::SMEM_COL : Sh::SMEM));
 }
 
 template <typename R, int L>
@@ -1659,12 +1926,15 @@ inline int prepare_one() {
     e2 = cudaFuncSetAttribute(pass_kernel_tma<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PShape<L, true>::SMEM);
     if constexpr (NSLCT_PAIR && is_pow2(L) && L >= 256) {
-      if (e1 == cudaSuccess)
-        e1 = cudaFuncSetAttribute(pass_kernel_pair<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)PairShape<L>::SMEM);
-      if (e2 == cudaSuccess)
-        e2 = cudaFuncSetAttribute(pass_kernel_pair<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)PairShape<L>::SMEM_COL);
+      if constexpr (NSLCT_PAIR_X2) {
+        if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 1>();
+        if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 2>();
+        if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 3>();
+        if (e2 == cudaSuccess) e2 = prepare_pair<L, true, 4>();
+      } else {
+        if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 0>();
+        if (e2 == cudaSuccess) e2 = prepare_pair<L, true, 0>();
+      }
     }
     if constexpr (is_pow2(L) && L >= 256) {
       if (e1 == cudaSuccess)

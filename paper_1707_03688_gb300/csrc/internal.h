@@ -22,6 +22,24 @@ struct Chirp {
 
 enum Transform : int { kNone = 0, kFwd = 1, kInv = 2 };
 
+// A pass of the packed line-pair kernel as a program: transforms T_0 ..
+// T_{ntr-1} of alternating direction, an optional step before T_0, one step in
+// each gap between transforms and up to two after the last. A step multiplies
+// by a chirp (times scale) or by scale alone; kind 0 is no step. Filled by the
+// launcher from the generic fields of PassDesc.
+struct X2Step {
+  int kind;            // 0 none, 1 chirp x scale, 2 scale
+  int freq;            // chirp indices: 0 = centred samples, 1 = centred bins
+  float scale;
+  Chirp c;
+};
+struct X2Prog {
+  int ntr;
+  X2Step pre;
+  X2Step gap[2];
+  X2Step post[2];
+};
+
 // One kernel pass: a batch of 1D transforms of length L along one axis, each
 // optionally followed by a chirp multiply and a second 1D transform.
 //   row pass: lines are rows i (length Ny), elements are columns j
@@ -71,6 +89,8 @@ struct PassDesc {
   // are copied, so that its wait must expire
   unsigned int wait_us;
   unsigned int test_extra_tx;
+  // the same pass as a program for the packed line-pair kernel (set by its launcher)
+  X2Prog x2;
 };
 
 // FP32 lines of 256..4096 points run in the line-pair kernel (which also
