@@ -1158,6 +1158,13 @@ bool encode_column_map_batched(CUtensorMap* map, const void* base, int Nx, int N
 // Waits are bounded as in v3.
 // ---------------------------------------------------------------------------
 // (NSLCT_PAIR: see internal.h)
+// packed pair kernel, row passes: the next panel's load is issued as soon as
+// the last FFT stage has read the buffer (1), or after the panel's work (0).
+// (Column passes load the next panel's halves as their TMA stores drain: an
+// early load of the lower half measured 1 % slower there.)
+#ifndef NSLCT_PAIR_EARLY_LOAD
+#define NSLCT_PAIR_EARLY_LOAD 1
+#endif
 // row passes of the pair kernel: 16-byte tiled loads and stores with a lane-pair shuffle
 #ifndef NSLCT_PAIR_SHFL
 #define NSLCT_PAIR_SHFL 1
@@ -1317,9 +1324,9 @@ template <int L> struct X2Fft {
 
   static __device__ __forceinline__ int sidx(int g, int e) { return g * Sh::LS + padded_by<SH>(e); }
 
-  template <int ST>
+  template <int ST, class Hook>
   static __device__ __forceinline__ void stage(cx2* v, ulonglong2* sm, int t, int g, const float2* __restrict__ tw,
-                                               const X2Const& K) {
+                                               const X2Const& K, const Hook& freed, bool call) {
     constexpr int RD = stage_radix(L, E, ST);
     constexpr int NS = stage_ns(L, E, ST);
     constexpr bool FIRST = (ST == 0);
@@ -1333,7 +1340,12 @@ template <int L> struct X2Fft {
         const ulonglong2 q = sm[sidx(g, t + T * s)];
         v[s] = cx2{q.x, q.y};
       }
-      if constexpr (!LAST) __syncthreads();
+      if constexpr (!LAST) {
+        __syncthreads();
+      } else if (call) {
+        __syncthreads();  // every thread has read the buffer for the last time
+        freed();
+      }
     }
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
@@ -1359,19 +1371,24 @@ template <int L> struct X2Fft {
     }
   }
 
-  template <int ST>
+  template <int ST, class Hook>
   static __device__ __forceinline__ void stages(cx2* v, ulonglong2* sm, int t, int g, const float2* __restrict__ tw,
-                                                const X2Const& K) {
+                                                const X2Const& K, const Hook& freed, bool call) {
     if constexpr (ST < S) {
-      stage<ST>(v, sm, t, g, tw, K);
-      stages<ST + 1>(v, sm, t, g, tw, K);
+      stage<ST>(v, sm, t, g, tw, K, freed, call);
+      stages<ST + 1>(v, sm, t, g, tw, K, freed, call);
     }
   }
 
-  static __device__ __forceinline__ void run(cx2* v, ulonglong2* sm, int t, int g, const float2* __restrict__ tw) {
+  // With `call`, freed() runs in every thread, after a barrier, as soon as the
+  // last stage has read the buffer (the caller reuses it, e.g. for the next
+  // panel's load, while the last stage computes).
+  template <class Hook>
+  static __device__ __forceinline__ void run(cx2* v, ulonglong2* sm, int t, int g, const float2* __restrict__ tw,
+                                             const Hook& freed, bool call) {
     const X2Const K;
     __syncthreads();  // the previous user of `sm` is done
-    stages<0>(v, sm, t, g, tw, K);
+    stages<0>(v, sm, t, g, tw, K, freed, call);
   }
 };
 
@@ -1547,6 +1564,17 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       }
       return;
     }
+    const int next = gp + gridDim.x;
+    const int nbf = next / npf;                          // the next panel's field
+    // thread 0 issues the next panel's copies into the freed buffer (row
+    // passes of the packed kernel: as soon as the last FFT stage has read it)
+    constexpr bool EARLY = MODE != 0 && NSLCT_PAIR_EARLY_LOAD && !COL;
+    auto load_next = [&]() {
+      if (tid == 0 && next < npanels) {
+        fence_proxy_async();
+        pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf);
+      }
+    };
     float2 v0[E], v1[E];
     if (COL) {
 #pragma unroll
@@ -1644,7 +1672,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
           const X2Step st = k == 1 ? d.x2.gap[0] : d.x2.gap[1];
           x2_step<L, COL, true>(v, st, FINV != (((k - 1) & 1) != 0), d, t, line0);
         }
-        X2Fft<L>::run(v, xs2, t, g, tw);
+        X2Fft<L>::run(v, xs2, t, g, tw, load_next, EARLY && k == d.x2.ntr - 1);
       }
       if (d.x2.post[0].kind) x2_step<L, COL, false>(v, d.x2.post[0], LINV, d, t, line0);
       if (d.x2.post[1].kind) x2_step<L, COL, false>(v, d.x2.post[1], LINV, d, t, line0);
@@ -1662,17 +1690,12 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         v1[s] = apply_post_mask<float>(d, line0 + 1, t + T * s, v1[s]);
       }
     }
-    __syncthreads();  // every thread has finished reading the buffer
-    const int next = gp + gridDim.x;
-    const int nbf = next / npf;                          // the next panel's field
+    if constexpr (!EARLY) __syncthreads();  // every thread has finished reading the buffer
 
     if constexpr (COL && !NSLCT_PAIR_COL_TMA_STORE) {
-      // next panel's load first, then 16-byte stores of (line0[e], line1[e]),
-      // one tile row of the column pair each
-      if (tid == 0 && next < npanels) {
-        fence_proxy_async();
-        pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf);
-      }
+      // next panel's load first (already issued when EARLY), then 16-byte
+      // stores of (line0[e], line1[e]), one tile row of the column pair each
+      if constexpr (!EARLY) load_next();
       if (valid) {
         float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll
@@ -1732,10 +1755,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
           pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf);
       }
     } else {
-      if (tid == 0 && next < npanels) {
-        fence_proxy_async();
-        pair_load_panel<L, COL>(xs, in0 + nbf * d.in_bstride, &map_in, d, (next % npf) * P, bar, nbf);
-      }
+      if constexpr (!EARLY) load_next();
       if (!d.out_tiled && d.pad_out) {
         // zero padding: store the output region alone
         const int r = line0 - d.out_r0;
