@@ -58,6 +58,10 @@ PASS_KERNELS = {
                    "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>"],
     ("mixed", 3): ["pass_kernel_tma<4096, 0, 1>", "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>"],
 }
+# the same for the batched kernel (256 fields {128..2048}^2, all batched; row
+# kernel: mean of passes 1, 3, 5) and the adjoint kernel (64 x 1024^2)
+NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 256>": 2.171e9, "batch_pass_kernel<1, 256>": 2.137e9}
+NCU_TRAFFIC_GRAD = {"dual_pass_kernel<float, 1024, 0>": 2.116e9, "dual_pass_kernel<float, 1024, 1>": 2.099e9}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
@@ -406,6 +410,36 @@ def _timed(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def _pass_times(run_pass, npass, iters, stream):
+    """Mean duration (ms) of each of npass passes, run in order `iters` times
+    with CUDA events between them on `stream`."""
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(iters)]
+    for e in evs:
+        e[0].record(stream)
+        for k in range(npass):
+            run_pass(k)
+            e[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return np.mean([[e[k].elapsed_time(e[k + 1]) for k in range(npass)] for e in evs], axis=0)
+
+
+def _dominant_roofline(pass_ms, names, bytes_launch, traffic=None):
+    """Roofline of the kernel (as ncu names it) with the largest share of the
+    passes' time: algorithmic bytes per launch over its mean launch time."""
+    per = {}
+    for j, name in enumerate(names):
+        tot, n = per.get(name, (0.0, 0))
+        per[name] = (tot + float(pass_ms[j]), n + 1)
+    dom = max(per, key=lambda k: per[k][0])
+    ms = per[dom][0] / per[dom][1]
+    peak, kind = _peaks()
+    achieved = bytes_launch / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (traffic or {}).get(dom), "kernel": dom, "share": per[dom][0] / float(np.sum(pass_ms)),
+            "peak_source": f"hbm_gbs ({kind})", "bytes_per_launch": bytes_launch, "avg_launch_ms": ms}
+
+
 def run_batch_workload(args, world, rank):
     """256 fields with Nx, Ny drawn from {128, ..., 2048}, each with its own ABCD:
     the batched persistent launches (captured in one CUDA graph) against the
@@ -429,6 +463,9 @@ def run_batch_workload(args, world, rank):
         ms_each = _timed(lambda: b.forward_each(stream), args.steps, args.warmup, stream)
         b.set_split(1 << 30)
         ms_all_batched = _timed(lambda: b.forward(stream), args.steps, args.warmup, stream)
+        # every field batched: each pass is one persistent launch over all samples
+        th_all = b.threads
+        pass_ms = _pass_times(lambda k: b.forward_pass(k, stream), 5, max(1, args.steps // 5), stream)
         split, _ = b.tune(stream, iters=2)
         ms_launch = _timed(lambda: b.forward(stream), args.steps, args.warmup, stream)
         b.capture(stream)
@@ -447,6 +484,11 @@ def run_batch_workload(args, world, rank):
         "all_batched_no_graph": {"ms_per_step": ms_all_batched, "value": samples / (ms_all_batched * 1e-3) / 1e6},
         "tuned_no_graph": {"ms_per_step": ms_launch, "value": samples / (ms_launch * 1e-3) / 1e6},
         "gpu_launches": 5 + 5 * sum(1 for nx, ny in shapes if min(nx, ny) >= split), "clocks": clk.summary(),
+        # the batched kernel with every field batched, passes timed one by one
+        "roofline": _dominant_roofline(pass_ms, [f"batch_pass_kernel<{int(chain_col)}, {th_all}>"
+                                                 for chain_col in (0, 1, 0, 1, 0)],
+                                       BYTES_PER_SAMPLE_PASS * samples, NCU_TRAFFIC_BATCH),
+        "pass_ms_all_batched": [round(float(v), 5) for v in pass_ms],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -564,6 +606,14 @@ def run_grad_workload(args, world, rank):
     with ClockSampler(torch.cuda.current_device()) as clk:
         ms = _timed(step, args.steps, args.warmup, stream)
     value = nb * n * n / (ms * 1e-3) / 1e6
+    # the forward alone, and the five dual passes of the backward one by one
+    ms_fwd = _timed(lambda: N.nslct_forward_many(plan.handle, x, y, stream), args.steps, args.warmup, stream)
+    pass_ms = _pass_times(lambda k: N.nslct_backward_pass(plan.handle, k, gy, y, gx, ws, stream), 5,
+                          max(1, args.steps // 5), stream)
+    # each dual pass reads and writes two complex64 fields (gradient and value paths)
+    roof = _dominant_roofline(pass_ms, [f"dual_pass_kernel<float, {n}, {c}>" for c in (0, 1, 0, 1, 0)],
+                              2 * BYTES_PER_SAMPLE_PASS * nb * n * n, NCU_TRAFFIC_GRAD)
+    roof["share"] = roof["share"] * float(np.sum(pass_ms)) / ms
     line = {
         "metric": "forward + backward (x and ABCD-parameter gradients) Msamples/s", "value": value,
         "unit": "Msamples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -573,6 +623,9 @@ def run_grad_workload(args, world, rank):
                                "nslct_forward_many + nslct_backward_many",
                    "note": "the residual 2(y - y_t) is formed with torch ops between the two library calls"},
         "gpu_launches": 5 + 5 + 1, "clocks": clk.summary(),
+        # share: of the whole step (forward, residual, backward, finalisation)
+        "roofline": roof,
+        "forward_ms": ms_fwd, "backward_pass_ms": [round(float(v), 5) for v in pass_ms],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

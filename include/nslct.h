@@ -311,6 +311,21 @@ int nslct_backward_many(nslct_plan_t plan, int nbatch, long long stride, const v
                         nslct_stream_t stream);
 
 /*
+ * nslct_backward_pass -- enqueue ONE of the five dual passes of
+ * nslct_backward_many (same arguments, pass 0..4), for profiling and per-pass
+ * timing. Each pass reads the previous pass's outputs:
+ *   pass 0: grad_out and y (row-major) -> grad_in and the value-path workspace
+ *   passes 1..4: grad_in and the workspace -> themselves
+ * In pass 4 grad_in returns to row-major. Calling passes 0..4 in order gives
+ * nslct_backward_many's grad_in. The per-CTA parameter sums land in the plan's
+ * partial-sum buffer but are never finalised: no gradient for theta or the
+ * chirps comes out of these calls. NSLCT_E_ARG for a pass outside 0..4,
+ * otherwise as nslct_backward_many.
+ */
+int nslct_backward_pass(nslct_plan_t plan, int pass, int nbatch, long long stride, const void* grad_out,
+                        const void* y, void* grad_in, void* workspace, nslct_stream_t stream);
+
+/*
  * nslct_plan_theta -- plan for M(theta) (see nslct_backward) with H = h0 moved
  * onto the feasible plane of M(theta) along its normal:
  *   h = h0 + r (rhs - r.h0) / (r.r),  r = (-a21, a11 - a22, a12), rhs = b12 - b21,
@@ -408,6 +423,17 @@ int nslct_batch_threads(nslct_batch_t batch);
  * the repeated runs would feed outputs back in. Drops a captured graph.
  */
 int nslct_batch_tune(nslct_batch_t batch, nslct_stream_t stream, int iters, int* chosen, float* ms_per_forward);
+
+/*
+ * nslct_batch_forward_pass -- enqueue ONE of the five passes of
+ * nslct_batch_forward (pass 0..4, as in nslct_forward_pass), for profiling and
+ * per-pass timing. The batched fields get one persistent launch; fields that
+ * run alone (see nslct_batch_set_split) get their own nslct_forward_pass, on
+ * `stream`. Calling passes 0..4 in order gives nslct_batch_forward's outputs.
+ * Does not use a captured graph. NSLCT_E_ARG if the batch is unbound or the
+ * pass is outside 0..4.
+ */
+int nslct_batch_forward_pass(nslct_batch_t batch, int pass, nslct_stream_t stream);
 
 /* nslct_batch_forward_each -- the same transforms as per-field nslct_forward calls (5 launches per field). */
 int nslct_batch_forward_each(nslct_batch_t batch, nslct_stream_t stream);

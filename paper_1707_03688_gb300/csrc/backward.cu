@@ -79,9 +79,10 @@ int dual_rows(const nslct_plan_s* p, int L, int nlines) {
 
 // Shared by nslct_backward and its variants: the five dual passes (writing
 // per-CTA sums to `partials`, `stride` rows per pass) and the finalisation.
+// only_pass in 0..4: that dual pass alone, without the finalisation.
 int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, void* grad_in, double* grad_theta,
                         double* grad_chirp, void* ws, double* partials, int stride, cudaStream_t s, int nbatch,
-                        long long fstride) {
+                        long long fstride, int only_pass) {
   const double nn = (double)p->Nx * (double)p->Ny;
   const double ccs = -1.0 / nn;
   PassDesc base{};
@@ -116,6 +117,7 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
   const bool want = grad_theta || grad_chirp;
   GradFinal f{};
   for (int k = 0; k < 5; ++k) {
+    if (only_pass >= 0 && k != only_pass) continue;
     const int acc = (want && k < 4) ? 1 : 0;
     if (acc) {
       const int L = cols[k] ? p->Nx : p->Ny;
@@ -126,7 +128,7 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
     const int rc = dual_launch(p, cols[k], d[k], in_y, ws, acc ? partials + (size_t)k * stride * 3 : nullptr, acc, s);
     if (rc != NSLCT_OK) return rc;
   }
-  if (!want) return NSLCT_OK;
+  if (!want || only_pass >= 0) return NSLCT_OK;
   // d loss / d chirp entry = -factor_s * sign_s * w_k * S_k, with w = (d1^2/2, d1 d2, d2^2/2)
   const double dwx = kTwoPi / (p->Nx * p->dx), dwy = kTwoPi / (p->Ny * p->dy);
   const double fs[4] = {1.0, 1.0 / nn, 1.0 / (nn * nn), 1.0 / nn};   // C1, B', C2, H
@@ -150,8 +152,8 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
 // are the plan's unless the caller passes a workspace; both grow on demand.
 static int backward_batch(nslct_plan_t p, int nbatch, long long fstride, const void* grad_out, const void* y,
                           void* grad_in, double* grad_theta, double* grad_chirp, void* workspace,
-                          nslct_stream_t stream) {
-  if (!p || !grad_out || !y || !grad_in || nbatch < 1) return NSLCT_E_ARG;
+                          nslct_stream_t stream, int only_pass = -1) {
+  if (!p || !grad_out || !y || !grad_in || nbatch < 1 || only_pass > 4) return NSLCT_E_ARG;
   if (p->padded || p->type2) return NSLCT_E_UNSUPPORTED;
   if (grad_theta && !p->has_theta) return NSLCT_E_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(grad_out) | reinterpret_cast<uintptr_t>(y) |
@@ -185,7 +187,8 @@ static int backward_batch(nslct_plan_t p, int nbatch, long long fstride, const v
   }
   if (rc == NSLCT_OK)
     rc = nslct_backward_impl(p, grad_out, y, grad_in, grad_theta, grad_chirp, workspace ? workspace : p->ws,
-                             p->partials, p->partials_stride, reinterpret_cast<cudaStream_t>(stream), nbatch, fstride);
+                             p->partials, p->partials_stride, reinterpret_cast<cudaStream_t>(stream), nbatch, fstride,
+                             only_pass);
   if (prev != p->device) cudaSetDevice(prev);
   return rc;
 }
@@ -199,4 +202,10 @@ extern "C" int nslct_backward_many(nslct_plan_t p, int nbatch, long long stride,
                                    void* grad_in, double* grad_theta, double* grad_chirp, void* workspace,
                                    nslct_stream_t stream) {
   return backward_batch(p, nbatch, stride, grad_out, y, grad_in, grad_theta, grad_chirp, workspace, stream);
+}
+
+extern "C" int nslct_backward_pass(nslct_plan_t p, int pass, int nbatch, long long stride, const void* grad_out,
+                                   const void* y, void* grad_in, void* workspace, nslct_stream_t stream) {
+  if (pass < 0 || pass > 4) return NSLCT_E_ARG;
+  return backward_batch(p, nbatch, stride, grad_out, y, grad_in, nullptr, nullptr, workspace, stream, pass);
 }

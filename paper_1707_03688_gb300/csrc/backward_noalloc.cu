@@ -20,7 +20,7 @@
 // defined in backward.cu
 int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, void* grad_in, double* grad_theta,
                         double* grad_chirp, void* ws, double* partials, int stride, cudaStream_t s, int nbatch,
-                        long long fstride);
+                        long long fstride, int only_pass);
 
 namespace {
 
@@ -65,7 +65,7 @@ extern "C" int nslct_backward_noalloc(nslct_plan_t p, const void* grad_out, void
   int rc = partials_address(p->device, &partials);
   if (rc == NSLCT_OK)
     rc = nslct_backward_impl(p, grad_out, y_inout, grad_in, grad_theta, grad_chirp, y_inout, partials, kNoallocRows,
-                             reinterpret_cast<cudaStream_t>(stream), 1, 0);
+                             reinterpret_cast<cudaStream_t>(stream), 1, 0, -1);
   if (prev != p->device) cudaSetDevice(prev);
   return rc;
 }

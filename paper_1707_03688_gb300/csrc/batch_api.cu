@@ -93,6 +93,18 @@ void drop_graph(nslct_batch_s* b) {
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
 }
 
+// Pass k of the batched fields: one persistent launch over its work items
+// (its counter must be zero).
+int launch_batched_pass(nslct_batch_s* b, int k, cudaStream_t s) {
+  if (b->nitems[k] == 0) return NSLCT_OK;
+  const int grid = std::min(b->nitems[k], (b->threads == 256 ? 2 : 1) * b->num_sms);
+  const PassDesc* descs = b->d_descs + (size_t)k * b->n;
+  const BatchItem* items = b->d_items + b->item_off[k];
+  return chain_pass_is_column(k)
+             ? launch_batch_col(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s)
+             : launch_batch_row(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s);
+}
+
 int enqueue(nslct_batch_s* b, cudaStream_t s) {
   // the large fields, each through its own fused passes, round-robin over the
   // side streams; the batched launches run on `s` meanwhile
@@ -109,13 +121,7 @@ int enqueue(nslct_batch_s* b, cudaStream_t s) {
   }
   if (cudaMemsetAsync(b->d_counters, 0, 5 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
   for (int k = 0; k < 5; ++k) {
-    if (b->nitems[k] == 0) continue;
-    const int grid = std::min(b->nitems[k], (b->threads == 256 ? 2 : 1) * b->num_sms);
-    const PassDesc* descs = b->d_descs + (size_t)k * b->n;
-    const BatchItem* items = b->d_items + b->item_off[k];
-    const int rc = chain_pass_is_column(k)
-                       ? launch_batch_col(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s)
-                       : launch_batch_row(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s);
+    const int rc = launch_batched_pass(b, k, s);
     if (rc != NSLCT_OK) return rc;
   }
   for (int k = 0; k < nside; ++k)
@@ -315,6 +321,18 @@ int nslct_batch_forward(nslct_batch_t b, nslct_stream_t stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (b->graph_exec) return cudaGraphLaunch(b->graph_exec, s) == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
   return enqueue(b, s);
+}
+
+int nslct_batch_forward_pass(nslct_batch_t b, int pass, nslct_stream_t stream) {
+  if (!b || !b->bound || pass < 0 || pass > 4) return NSLCT_E_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int f = 0; f < b->n; ++f) {
+    if (!runs_alone(b, f)) continue;
+    const int rc = nslct_forward_pass(b->plans[f], pass, b->in[f], b->out[f], stream);
+    if (rc != NSLCT_OK) return rc;
+  }
+  if (cudaMemsetAsync(b->d_counters + pass, 0, sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
+  return launch_batched_pass(b, pass, s);
 }
 
 int nslct_batch_forward_each(nslct_batch_t b, nslct_stream_t stream) {

@@ -46,12 +46,13 @@ EXPORTED = (
     "nslct_plan_padded", "nslct_plan_shape",
     "nslct_forward", "nslct_forward_masked", "nslct_forward_group", "nslct_inverse", "nslct_forward_many",
     "nslct_inverse_many",
-    "nslct_backward_many", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward", "nslct_backward_noalloc",
+    "nslct_backward_many", "nslct_backward_pass", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward",
+    "nslct_backward_noalloc",
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
     "nslct_batch_threads",
-    "nslct_batch_tune", "nslct_batch_forward_each", "nslct_batch_destroy",
+    "nslct_batch_tune", "nslct_batch_forward_pass", "nslct_batch_forward_each", "nslct_batch_destroy",
     "nslct_status", "nslct_selftest_timeout", "nslct_destroy", "nslct_strerror", "nslct_version",
 )
 
@@ -107,6 +108,9 @@ def load(path: str | None = None):
         "nslct_backward_many": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong, _VP, _VP, _VP, _VP, _VP, _VP,
                                                _VP]),
         "nslct_forward_pass": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+        "nslct_backward_pass": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _VP, _VP, _VP,
+                                               _VP, _VP]),
+        "nslct_batch_forward_pass": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
         "nslct_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "nslct_backward_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "nslct_plan_theta": (ctypes.c_int, [ctypes.POINTER(_VP), _PD, _PD, ctypes.c_int, ctypes.c_int, _D, _D,
@@ -308,6 +312,15 @@ def nslct_backward_many(plan: int, grad_out, y, grad_in, grad_theta=None, grad_c
     _check(load().nslct_backward_many(_VP(plan), int(grad_out.shape[0]), int(grad_out.stride(0)), _ptr(grad_out),
                                       _ptr(y), _ptr(grad_in), _ptr(grad_theta), _ptr(grad_chirp), _ptr(workspace),
                                       _stream_ptr(stream, grad_in.device)), "nslct_backward_many")
+    return grad_in
+
+
+def nslct_backward_pass(plan: int, k: int, grad_out, y, grad_in, workspace=None, stream=None):
+    """Enqueue dual pass k (0..4) of nslct_backward_many on [B, rows, cols]
+    tensors (profiling / per-pass timing; no parameter gradients)."""
+    _check(load().nslct_backward_pass(_VP(plan), int(k), int(grad_out.shape[0]), int(grad_out.stride(0)),
+                                      _ptr(grad_out), _ptr(y), _ptr(grad_in), _ptr(workspace),
+                                      _stream_ptr(stream, grad_in.device)), "nslct_backward_pass")
     return grad_in
 
 
@@ -622,6 +635,13 @@ class Batch:
         _check(load().nslct_batch_tune(_VP(self.handle), _stream_ptr(stream, torch.cuda.current_device()),
                                        int(iters), ctypes.byref(chosen), ctypes.byref(ms)), "nslct_batch_tune")
         return chosen.value, ms.value
+
+    def forward_pass(self, k: int, stream=None):
+        """Enqueue pass k (0..4) of the batch's forward (profiling / per-pass timing)."""
+        import torch
+        _check(load().nslct_batch_forward_pass(_VP(self.handle), int(k),
+                                               _stream_ptr(stream, torch.cuda.current_device())),
+               "nslct_batch_forward_pass")
 
     def forward_each(self, stream=None):
         import torch

@@ -178,6 +178,10 @@ def test_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.nslct_batch_tune(vp(0), vp(0), 1, None, None) == N.NSLCT_E_ARG
     assert lib.nslct_batch_set_split(vp(0), 4) == N.NSLCT_E_ARG
     assert lib.nslct_batch_threads(vp(0)) == 0
+    # single passes: a null plan or batch, a pass outside 0..4
+    assert lib.nslct_backward_pass(vp(0), 0, 1, 0, vp(0), vp(0), vp(0), vp(0), vp(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_backward_pass(vp(0), 5, 1, 0, vp(0), vp(0), vp(0), vp(0), vp(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_batch_forward_pass(vp(0), 0, vp(0)) == N.NSLCT_E_ARG
     # batches: an unsupported size is refused before any plan is made
     nx = (ctypes.c_int * 1)(100)
     ny = (ctypes.c_int * 1)(128)

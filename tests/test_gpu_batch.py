@@ -91,6 +91,27 @@ def test_batch_graph_and_each_agree(N, batch_case):
         assert O.rel_l2(o.cpu().numpy().astype(np.complex128), a.cpu().numpy().astype(np.complex128)) < 2e-6
 
 
+def test_batch_pass_sequence_equals_forward(N, batch_case):
+    """Passes 0..4 enqueued one by one give nslct_batch_forward's outputs
+    exactly, with every field batched and with the large ones run alone."""
+    b, shapes, abcds, fields, ins, outs = batch_case
+    for split in (1 << 30, 512):
+        b.set_split(split)
+        b.forward()
+        torch.cuda.synchronize()
+        ref = [o.clone() for o in outs]
+        for o in outs:
+            o.zero_()
+        for k in range(5):
+            b.forward_pass(k)
+        torch.cuda.synchronize()
+        for k, (a, o) in enumerate(zip(ref, outs)):
+            assert torch.equal(a, o), (split, k)
+    with pytest.raises(N.NslctError) as exc:
+        b.forward_pass(5)
+    assert exc.value.code == N.NSLCT_E_ARG
+
+
 def test_batch_rejects_unsupported_sizes(N):
     with pytest.raises(N.NslctError) as exc:
         N.Batch([I.random_symplectic_abcd(1)], [(48, 64)])

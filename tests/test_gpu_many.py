@@ -92,6 +92,29 @@ def test_backward_many_sums_parameter_gradients(N, precision):
     assert float(torch.linalg.vector_norm(gch - sch) / torch.linalg.vector_norm(sch)) < tol
 
 
+def test_backward_pass_sequence_equals_backward_many(N):
+    """Dual passes 0..4 enqueued one by one give nslct_backward_many's grad_in
+    exactly (the same launches); a pass outside 0..4 is refused."""
+    nx = ny = 256
+    plan = N.Plan(I.random_symplectic_abcd(13), nx, ny)
+    x = _batch(3, nx, ny, plan.dtype, seed=90)
+    y = plan.forward(x)
+    gy = 2 * (y - _batch(3, nx, ny, plan.dtype, seed=95))
+    gx = torch.empty_like(gy)
+    ws = torch.empty_like(gy)
+    N.nslct_backward_many(plan.handle, gy, y, gx, workspace=ws)
+    ref = gx.clone()
+    gx.zero_()
+    for k in range(5):
+        N.nslct_backward_pass(plan.handle, k, gy, y, gx, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(gx, ref)
+    with pytest.raises(N.NslctError) as exc:
+        N.nslct_backward_pass(plan.handle, 5, gy, y, gx, workspace=ws)
+    assert exc.value.code == N.NSLCT_E_ARG
+    plan.close()
+
+
 def test_autograd_batch(N):
     from paper_1707_03688_gb300.autograd import nslct_transform
     nx = ny = 64
