@@ -22,24 +22,49 @@
 namespace nslct {
 
 // Reduce the per-CTA sums in a fixed order (deterministic) and form the
-// 12 chirp gradients and, optionally, the 10 theta gradients.
-__global__ void __launch_bounds__(256) grad_finalize_kernel(const double* __restrict__ partials, GradFinal f,
-                                                            double* grad_chirp, double* grad_theta) {
-  __shared__ double red[256];
+// 12 chirp gradients and, optionally, the 10 theta gradients. Each thread
+// sums whole rows (S_aa, S_ab, S_bb) of every slot, rows t, t + T, ... in
+// four independent chains (loads in flight) added in a fixed order; then the
+// warps and the block reduce in a fixed tree.
+constexpr int kFinalizeThreads = 1024;
+__global__ void __launch_bounds__(kFinalizeThreads) grad_finalize_kernel(const double* __restrict__ partials,
+                                                                         GradFinal f, double* grad_chirp,
+                                                                         double* grad_theta) {
+  __shared__ double red[kFinalizeThreads / 32][12];
   __shared__ double sums[12];
-  for (int slot = 0; slot < 4; ++slot)
-    for (int k = 0; k < 3; ++k) {
-      double acc = 0.0;
-      for (int b = threadIdx.x; b < f.nblk[slot]; b += blockDim.x) acc += partials[((size_t)slot * f.stride + b) * 3 + k];
-      red[threadIdx.x] = acc;
-      __syncthreads();
-      for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) sums[slot * 3 + k] = red[0] * f.factor[slot][k];
-      __syncthreads();
-    }
+  double acc[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+#pragma unroll
+  for (int slot = 0; slot < 4; ++slot) {
+    const double* __restrict__ rows = partials + (size_t)slot * f.stride * 3;
+    double c[4][3] = {};
+    int b = threadIdx.x;
+    for (; b + 3 * kFinalizeThreads < f.nblk[slot]; b += 4 * kFinalizeThreads)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c[u][k] += rows[(size_t)(b + u * kFinalizeThreads) * 3 + k];
+    for (; b < f.nblk[slot]; b += kFinalizeThreads)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) c[0][k] += rows[(size_t)b * 3 + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[slot * 3 + k] = (c[0][k] + c[1][k]) + (c[2][k] + c[3][k]);
+  }
+#pragma unroll
+  for (int q = 0; q < 12; ++q)
+    for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) red[warp][q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    double tot = 0.0;
+    for (int w = 0; w < kFinalizeThreads / 32; ++w) tot += red[w][threadIdx.x];
+    sums[threadIdx.x] = tot * f.factor[threadIdx.x / 3][threadIdx.x % 3];
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     // slots: 0 = C1, 1 = B', 2 = C2, 3 = H; output order H, B', C1, C2
     double g[12];
@@ -143,7 +168,7 @@ int nslct_backward_impl(nslct_plan_t p, const void* grad_out, const void* y, voi
   f.stride = stride;
   f.want_theta = (grad_theta && p->has_theta) ? 1 : 0;
   std::memcpy(f.jac, p->jac, sizeof(f.jac));
-  grad_finalize_kernel<<<1, 256, 0, s>>>(partials, f, grad_chirp, grad_theta);
+  grad_finalize_kernel<<<1, kFinalizeThreads, 0, s>>>(partials, f, grad_chirp, grad_theta);
   return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
 }
 

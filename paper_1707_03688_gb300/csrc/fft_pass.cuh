@@ -1976,6 +1976,141 @@ inline int prepare_one() {
 
 namespace nslct {
 
+// The adjoint's two paths through one packed FFT (pair_x2.cuh): lane 0 holds a
+// line of the gradient path, lane 1 the same line of the value path, P lines
+// interleaved thread by thread as in LineFft2. Twiddles come from the full
+// table (correctly rounded, as in LineFft2), broadcast to both lanes.
+#ifndef NSLCT_DUAL_X2
+#define NSLCT_DUAL_X2 1
+#endif
+template <int L, int P, int E_>
+struct LineFftX2 {
+  static constexpr int E = E_;
+  static constexpr int T_LINE = L / E;
+  static constexpr int S = num_stages(L, E);
+  static constexpr int SH = pad_shift(E);
+  static __device__ __forceinline__ int sidx(int p, int e) { return padded_by<SH>(e) * P + p; }
+
+  template <int ST>
+  static __device__ __forceinline__ void stage(cx2* v, ulonglong2* sm, int t, int p, const float2* __restrict__ tw,
+                                               const X2Const& K) {
+    constexpr int RD = stage_radix(L, E, ST);
+    constexpr int NS = stage_ns(L, E, ST);
+    constexpr bool FIRST = (ST == 0);
+    constexpr bool LAST = (ST == S - 1);
+    constexpr int NB = E / RD;
+    if constexpr (!FIRST) {
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const ulonglong2 q = sm[sidx(p, t + T_LINE * s)];
+        v[s] = cx2{q.x, q.y};
+      }
+      if constexpr (!LAST) __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      cx2 x[RD];
+#pragma unroll
+      for (int r = 0; r < RD; ++r) x[r] = v[u + r * NB];
+      const int j = t + u * T_LINE;
+      const int jm = j % NS;
+      if constexpr (NS > 1) {
+        float2 w[RD];
+        load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+#pragma unroll
+        for (int r = 1; r < RD; ++r) x[r] = tw2_apply(x[r], tw2_from(w[r]));
+      }
+      X2Dft<RD>::run(x, K);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < RD; ++r) v[u + r * NB] = x[r];
+      } else {
+        const int base = (j / NS) * NS * RD + jm;
+#pragma unroll
+        for (int r = 0; r < RD; ++r) sm[sidx(p, base + r * NS)] = make_ulonglong2(x[r].re, x[r].im);
+      }
+    }
+  }
+
+  template <int ST>
+  static __device__ __forceinline__ void stages(cx2* v, ulonglong2* sm, int t, int p, const float2* __restrict__ tw,
+                                                const X2Const& K) {
+    if constexpr (ST < S) {
+      stage<ST>(v, sm, t, p, tw, K);
+      stages<ST + 1>(v, sm, t, p, tw, K);
+    }
+  }
+
+  // unnormalised DFT, or the inverse as conj(DFT(conj x)), of both paths
+  static __device__ __forceinline__ void run(float2* a, float2* b, ulonglong2* sm, int t, int p,
+                                             const float2* __restrict__ tw, bool inverse) {
+    const X2Const K;
+    const f32x2 sg = x2_bcast(inverse ? -1.0f : 1.0f);
+    cx2 v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = cx2{x2_pack(a[s].x, b[s].x), x2_mul(x2_pack(a[s].y, b[s].y), sg)};
+    if constexpr (S > 1) __syncthreads();
+    stages<0>(v, sm, t, p, tw, K);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      x2_unpack(v[s].re, a[s].x, b[s].x);
+      x2_unpack(x2_mul(v[s].im, sg), a[s].y, b[s].y);
+    }
+  }
+};
+
+// dual kernels whose line length the packed codelets cover
+template <int L> __host__ __device__ constexpr bool dual_x2_length() {
+  if constexpr (!NSLCT_DUAL_X2 || !is_pow2(L) || L < 16) return false;
+  else {
+    constexpr int E = elems_per_thread(L);
+    bool ok = true;
+    for (int st = 0; st < num_stages(L, E); ++st) {
+      const int r = stage_radix(L, E, st);
+      ok = ok && (r == 2 || r == 4 || r == 8 || r == 16);
+    }
+    return ok;
+  }
+}
+
+// Multiply both paths' values of one line by the pass chirp times scale: one
+// chirp value per element (phases exactly as in apply_chirp_c), broadcast to
+// both lanes.
+template <int L, bool COL, int E>
+__device__ __forceinline__ void x2_dual_chirp(float2* a, float2* b, const PassDesc& d, int t, int line, float scale) {
+  constexpr int T = L / E;
+  const Chirp& ch = d.chirp;
+  const int nl = COL ? d.Ny : d.Nx;
+  const long long bl = d.freq_domain ? (long long)centred_bin(line, nl) : (long long)line - nl / 2;
+  const long long a0 = d.freq_domain ? (long long)t : (long long)t - L / 2;
+  const uint64_t ka = COL ? ch.k11 : ch.k22;
+  const uint64_t kb = COL ? ch.k22 : ch.k11;
+  const uint64_t kab_b = ch.k12 * (uint64_t)bl;
+  const uint64_t base = kb * (uint64_t)(bl * bl);
+  const uint64_t dd = 2ull * ka * (uint64_t)((long long)T * T);
+  uint64_t q = ka * (uint64_t)(a0 * a0) + kab_b * (uint64_t)a0 + base;
+  uint64_t dq = ka * (uint64_t)(2 * a0 * T + (long long)T * T) + kab_b * (uint64_t)T;
+#pragma unroll
+  for (int s = 0; s < E; ++s) {
+    if (d.freq_domain && s == E / 2) {
+      const long long av = a0 + (long long)T * s - L;
+      q = ka * (uint64_t)(av * av) + kab_b * (uint64_t)av + base;
+      dq = ka * (uint64_t)(2 * av * T + (long long)T * T) + kab_b * (uint64_t)T;
+    }
+    const float tt = (float)(int)(unsigned)(q >> 32) * 2.3283064365386963e-10f;  // 2^-32
+    float sn, cs;
+    __sincosf(6.28318530717958647692f * tt, &sn, &cs);
+    q += dq;
+    dq += dd;
+    const float2 w = make_float2(cs * scale, sn * scale);
+    const cx2 x = {x2_pack(a[s].x, b[s].x), x2_pack(a[s].y, b[s].y)};
+    const cx2 y = tw2_apply(x, tw2_from(w));
+    x2_unpack(y.re, a[s].x, b[s].x);
+    x2_unpack(y.im, a[s].y, b[s].y);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Dual passes for the adjoint (nslct_backward). Two fields go through the same
 // pass of the inverse chain: the gradient path g (-> grad_in) and the value
@@ -2040,8 +2175,11 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
     vg[s] = valid ? gin[k] : mk<R>((R)0, (R)0);
     vy[s] = valid ? yin[k] : mk<R>((R)0, (R)0);
   }
+  constexpr bool X2 = sizeof(R) == 4 && dual_x2_length<L>();
   if (d.t1 != kNone) {
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (X2) {
+      LineFftX2<L, P, E>::run(vg, vy, reinterpret_cast<ulonglong2*>(sm), t, p, tw, d.t1 == kInv);
+    } else if constexpr (sizeof(R) == 4) {
       LineFft2<L, P, E>::run(vg, vy, reinterpret_cast<float4*>(sm), t, p, tw, d.t1 == kInv);
     } else {
       LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t1 == kInv);
@@ -2094,8 +2232,12 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
     }
   }
   if (d.has_chirp) {
-    apply_chirp<R, L, COL, E>(vg, d, t, line, (R)d.scale);
-    apply_chirp<R, L, COL, E>(vy, d, t, line, (R)d.scale);
+    if constexpr (X2) {
+      x2_dual_chirp<L, COL, E>(vg, vy, d, t, line, (float)d.scale);
+    } else {
+      apply_chirp<R, L, COL, E>(vg, d, t, line, (R)d.scale);
+      apply_chirp<R, L, COL, E>(vy, d, t, line, (R)d.scale);
+    }
   } else if (d.scale != 1.0) {
     const R scale = (R)d.scale;
 #pragma unroll
@@ -2105,7 +2247,9 @@ dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, in
     }
   }
   if (d.t2 != kNone) {
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (X2) {
+      LineFftX2<L, P, E>::run(vg, vy, reinterpret_cast<ulonglong2*>(sm), t, p, tw, d.t2 == kInv);
+    } else if constexpr (sizeof(R) == 4) {
       LineFft2<L, P, E>::run(vg, vy, reinterpret_cast<float4*>(sm), t, p, tw, d.t2 == kInv);
     } else {
       LineFft<R, L, P, E, false, true>::run(vg, sm, t, p, tw, d.t2 == kInv);
