@@ -61,7 +61,7 @@ PASS_KERNELS = {
 # the same for the batched kernel (256 fields {128..2048}^2, all batched; row
 # kernel: mean of passes 1, 3, 5) and the adjoint kernel (64 x 1024^2)
 NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 256>": 2.171e9, "batch_pass_kernel<1, 256>": 2.137e9}
-NCU_TRAFFIC_GRAD = {}
+NCU_TRAFFIC_GRAD = {"dual_pass_kernel<float, 1024, 0>": 2.088e9, "dual_pass_kernel<float, 1024, 1>": 2.089e9}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
 WORKLOAD = ("4096x4096 complex64 field (8 Gaussian blobs + 5% complex white noise), 16 random "
