@@ -1,4 +1,5 @@
 // C ABI of libnslct (declared in include/nslct.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -595,8 +596,13 @@ struct SideStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
 };
+// streams nslct_forward_group spreads its transforms over (the caller's + side streams)
+#ifndef NSLCT_GROUP_STREAMS
+#define NSLCT_GROUP_STREAMS 2
+#endif
+static_assert(NSLCT_GROUP_STREAMS >= 2 && NSLCT_GROUP_STREAMS <= 8, "group streams");
 static std::mutex g_side_mu;
-static SideStream g_side[64];
+static SideStream g_side[64][NSLCT_GROUP_STREAMS - 1];
 
 int nslct_forward_group(int n, const nslct_plan_t* plans, const void* const* in, void* const* out,
                         nslct_stream_t stream) {
@@ -609,25 +615,31 @@ int nslct_forward_group(int n, const nslct_plan_t* plans, const void* const* in,
   if (!g.ok) return NSLCT_E_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (n == 1) return nslct_forward(plans[0], in[0], out[0], stream);
-  SideStream* ss = &g_side[dev];
+  const int nside = std::min(n, NSLCT_GROUP_STREAMS) - 1;
+  SideStream* ss = g_side[dev];
   {
     std::lock_guard<std::mutex> lock(g_side_mu);
-    if (!ss->s) {
-      if (cudaStreamCreateWithFlags(&ss->s, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming) != cudaSuccess)
+    for (int i = 0; i < nside; ++i) {
+      if (ss[i].s) continue;
+      if (cudaStreamCreateWithFlags(&ss[i].s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ss[i].fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ss[i].join, cudaEventDisableTiming) != cudaSuccess)
         return NSLCT_E_CUDA;
     }
   }
-  // transforms 0, 2, 4, ... on the caller's stream, 1, 3, ... on the side
-  // stream, forked from and joined back to the caller's stream
-  if (cudaEventRecord(ss->fork, s) != cudaSuccess || cudaStreamWaitEvent(ss->s, ss->fork, 0) != cudaSuccess)
-    return NSLCT_E_CUDA;
+  // transform k on stream k mod (nside + 1): the caller's stream, then the
+  // side streams, each forked from and joined back to the caller's stream
+  for (int i = 0; i < nside; ++i)
+    if (cudaEventRecord(ss[i].fork, s) != cudaSuccess || cudaStreamWaitEvent(ss[i].s, ss[i].fork, 0) != cudaSuccess)
+      return NSLCT_E_CUDA;
   int rc = NSLCT_OK;
-  for (int k = 0; k < n && rc == NSLCT_OK; ++k)
-    rc = nslct_forward(plans[k], in[k], out[k], k % 2 == 0 ? stream : reinterpret_cast<nslct_stream_t>(ss->s));
-  if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(s, ss->join, 0) != cudaSuccess)
-    return NSLCT_E_CUDA;
+  for (int k = 0; k < n && rc == NSLCT_OK; ++k) {
+    const int j = k % (nside + 1);
+    rc = nslct_forward(plans[k], in[k], out[k], j == 0 ? stream : reinterpret_cast<nslct_stream_t>(ss[j - 1].s));
+  }
+  for (int i = 0; i < nside; ++i)
+    if (cudaEventRecord(ss[i].join, ss[i].s) != cudaSuccess || cudaStreamWaitEvent(s, ss[i].join, 0) != cudaSuccess)
+      return NSLCT_E_CUDA;
   return rc;
 }
 
