@@ -238,7 +238,8 @@ def run_gpu(args, world, rank, local):
     N.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     g, mats = _make_inputs()
-    plans = [N.Plan(m, NX, NY, precision=args.precision, method=args.method) for m in mats]
+    plans = [N.Plan(m, NX, NY, precision=args.precision, method=args.method, decomposition=args.decomposition)
+             for m in mats]
     npass = plans[0].passes()
     if any(p.passes() != npass for p in plans):
         raise RuntimeError("plans of one bench run must share their pass count")
@@ -355,7 +356,8 @@ def run_gpu(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16-split+f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.method == "ha" else WORKLOAD.replace("HA-NsDLCT", "LC-NsDLCT"),
+        "config": {"workload": (WORKLOAD if args.method == "ha" else WORKLOAD.replace("HA-NsDLCT", "LC-NsDLCT"))
+                   + ("" if args.decomposition == "type1" else f", decomposition {args.decomposition}"),
                    "nx": NX, "ny": NY, "n_abcd": N_ABCD, "precision": args.precision,
                    "h_choice": H_CHOICE[args.method], "passes": npass, "parallelism": f"replicas x{world}",
                    "streams": "nslct_forward_group: the 16 independent transforms alternate over two CUDA streams",
@@ -378,9 +380,15 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import nslct_oracle as O
         p0 = plans[0]
-        params = O.decompose(p0.info()["abcd"], p0.params()["H"])
-        t0 = time.perf_counter()
-        ref = O.forward(g, params, p0.dx, p0.dy)
+        if p0.info()["flags"] & N.NSLCT_TYPE2:
+            # a type-2 plan reports the type-1 factors of M^-1 with H = -H1
+            params = O.decompose_type2(p0.info()["abcd"], -p0.params()["H"])
+            t0 = time.perf_counter()
+            ref = O.forward_type2(g, params, p0.dx, p0.dy)
+        else:
+            params = O.decompose(p0.info()["abcd"], p0.params()["H"])
+            t0 = time.perf_counter()
+            ref = O.forward(g, params, p0.dx, p0.dy)
         t_cpu = time.perf_counter() - t0
         gpu_out = outs[0].cpu().numpy().astype(np.complex128)
         result["rel_l2"] = {f"{args.precision}_vs_oracle": O.rel_l2(gpu_out, ref), "field": "ABCD seed 200, 4096^2",
@@ -645,6 +653,8 @@ def main():
                          "grad: 64 x 1024^2 forward + backward; filter: two-domain filtering, Eqs. Add04/Add08")
     ap.add_argument("--method", default="ha", choices=["ha", "lc_y"],
                     help="H of Eq. HA24 (five passes) or of Eq. LC10 (three passes)")
+    ap.add_argument("--decomposition", default="type1", choices=["type1", "type2", "trace"],
+                    help="CM-CC-CM-CC (Eq. HA28), CC-CM-CC-CM (Eq. CCCMCCCM16) or the tr(B) rule (Eq. Reversible08)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
                     help="fp32: FP32 FFT arithmetic; mixed: radix-16 stages as split-FP16 tensor-core DFT-16")
     ap.add_argument("--n-abcd", type=int, default=16,
