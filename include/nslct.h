@@ -409,8 +409,16 @@ int nslct_batch_capture(nslct_batch_t batch, nslct_stream_t stream);
 int nslct_batch_set_split(nslct_batch_t batch, int split);
 int nslct_batch_get_split(nslct_batch_t batch);
 /* nslct_batch_threads -- the CTA size of the batched kernels: 256 (two CTAs per
- * SM; the default when every line is at most 2048 points) or 512. */
+ * SM; the default when every line is at most 2048 points), 512, or 128 (three
+ * CTAs per SM, power-of-two lines as packed pairs; chosen only by
+ * nslct_batch_tune). */
 int nslct_batch_threads(nslct_batch_t batch);
+/* nslct_batch_set_threads -- pin the batched kernels' CTA size (128, 256 or
+ * 512, else NSLCT_E_ARG). NSLCT_E_SIZE if some field has a line that size does
+ * not handle (256: lines up to 2048; 128: up to 2048, power-of-two lines
+ * packed in pairs). Drops a captured graph; a later nslct_batch_tune may
+ * change it again. */
+int nslct_batch_set_threads(nslct_batch_t batch, int threads);
 
 /*
  * nslct_batch_tune -- autotune the split and the batched kernels' CTA size on

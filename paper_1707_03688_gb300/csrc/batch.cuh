@@ -19,15 +19,20 @@ namespace nslct {
 #define NSLCT_BATCH_LENGTHS(X) \
   X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(96) X(192) X(384) X(768) X(1536)
 
-// Two CTA sizes: 512 threads (one CTA per SM, every length) and 256 threads
+// Three CTA sizes: 512 threads (one CTA per SM, every length), 256 threads
 // (two CTAs per SM with independent barriers, lines up to 2048: a panel needs
-// at least two lines of L/E threads each).
+// at least two lines of L/E threads each) and 128 threads (three CTAs per SM).
+// With 128 threads, power-of-two lines up to 2048 run packed: each thread
+// holds the same positions of two lines as the two FP32x2 lanes
+// (pair_x2.cuh, LineFftX2), so a panel has twice the lines of its threads.
+template <int L, int TH> constexpr bool batch_packed() { return TH == 128 && dual_x2_length<L>() && L <= 2048; }
 template <int L, int TH> struct BShape {
   static constexpr int E = elems_per_thread(L);  // the plans' tw16 tables
   static constexpr int T_LINE = L / E;
   static constexpr int THREADS = TH;
-  static constexpr int P = TH / T_LINE;        // lines per panel
-  static constexpr bool ok = P >= 2 && P % 2 == 0 && P * T_LINE == TH;
+  static constexpr bool PACKED = batch_packed<L, TH>();
+  static constexpr int P = (PACKED ? 2 : 1) * TH / T_LINE;  // lines per panel
+  static constexpr bool ok = P >= 2 && P % 2 == 0 && (PACKED ? P / 2 : P) * T_LINE == TH;
   static constexpr int XSM = P * (L + L / 16);
   static constexpr int STG_ROW = P * (L + 8);  // row-major rows are padded in staging
   static constexpr int STG_TILED = P * L;
@@ -55,6 +60,7 @@ __host__ __device__ constexpr int batch_stg() {
 template <int TH> constexpr size_t batch_smem() { return (size_t)(batch_xsm<TH>() + batch_stg<TH>()) * sizeof(float2); }
 static_assert(batch_smem<512>() <= 227 * 1024, "batched kernel shared memory");
 static_assert(batch_smem<256>() <= 113 * 1024, "two 256-thread batched CTAs per SM");
+static_assert(batch_smem<128>() <= 74 * 1024, "three 128-thread batched CTAs per SM");
 
 // lines per panel for line length L with TH-thread CTAs (0: not handled)
 template <int TH>
@@ -164,10 +170,68 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
   }
 }
 
+// bprocess for packed panels: thread (pair q, position group t) holds lines
+// 2q and 2q + 1 at positions t + T_LINE s; both lines' FFTs run as one packed
+// FFT, the chirp per line.
+template <int L, bool COL, int TH>
+__device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2* stg, float2* xs,
+                                            const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items,
+                                            int next, int nitems) {
+  using Sh = BShape<L, TH>;
+  constexpr int E = Sh::E;
+  constexpr int T_LINE = Sh::T_LINE;
+  constexpr int P = Sh::P;
+  constexpr int PP = P / 2;  // line pairs per panel
+  const int tid = threadIdx.x;
+  const int q = tid % PP;
+  const int t = tid / PP;
+  const int nlines = COL ? d.Ny : d.Nx;
+  const int line0 = panel * P + 2 * q;
+  float2 a[E], b[E];
+#pragma unroll
+  for (int s = 0; s < E; ++s) {
+    a[s] = stg[bstg_index<L, COL, TH>(2 * q, t + T_LINE * s, d.in_tiled)];
+    b[s] = stg[bstg_index<L, COL, TH>(2 * q + 1, t + T_LINE * s, d.in_tiled)];
+  }
+  __syncthreads();  // staging consumed
+  if (next < nitems) {
+    const BatchItem it = items[next];
+    bstage_any<COL, TH>(stg, descs[it.field], it.panel);
+  }
+  const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
+  ulonglong2* xs2 = reinterpret_cast<ulonglong2*>(xs);
+  if (d.t1 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t1 == kInv);
+  if (d.has_chirp) {
+    apply_chirp<float, L, COL, E>(a, d, t, line0, d.fscale);
+    apply_chirp<float, L, COL, E>(b, d, t, line0 + 1, d.fscale);
+  } else if (d.scale_only) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      a[s] = make_float2(a[s].x * d.fscale, a[s].y * d.fscale);
+      b[s] = make_float2(b[s].x * d.fscale, b[s].y * d.fscale);
+    }
+  }
+  if (d.t2 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t2 == kInv);
+  float2* out = reinterpret_cast<float2*>(d.out);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int line = line0 + h;
+    if (line < nlines) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        const int e = t + T_LINE * s;
+        const int i = COL ? e : line;
+        const int j = COL ? line : e;
+        out[elem_index(i, j, d.Ny, d.out_tiled)] = h ? b[s] : a[s];
+      }
+    }
+  }
+}
+
 // One pass of the batch. descs[f] is field f's descriptor for this pass;
 // items[0..nitems) the work list; *counter must be 0 at launch.
 template <bool COL, int TH>
-__global__ void __launch_bounds__(TH, TH <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(TH, TH == 128 ? 3 : (TH <= 256 ? 2 : 1))
 batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item[2];
@@ -200,9 +264,14 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
     const PassDesc& d = s_desc;
     const int L = COL ? d.Nx : d.Ny;
     switch (L) {
-#define NSLCT_BCASE(LL)                                                                 \
-  case LL:                                                                              \
-    if constexpr (BShape<LL, TH>::ok) bprocess<LL, COL, TH>(d, it.panel, stg, xs, descs, items, next, nitems); \
+#define NSLCT_BCASE(LL)                                                                   \
+  case LL:                                                                                \
+    if constexpr (BShape<LL, TH>::ok) {                                                   \
+      if constexpr (BShape<LL, TH>::PACKED)                                               \
+        bprocess_x2<LL, COL, TH>(d, it.panel, stg, xs, descs, items, next, nitems);       \
+      else                                                                                \
+        bprocess<LL, COL, TH>(d, it.panel, stg, xs, descs, items, next, nitems);          \
+    }                                                                                     \
     break;
       NSLCT_BATCH_LENGTHS(NSLCT_BCASE)
 #undef NSLCT_BCASE
@@ -217,7 +286,9 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
 template <bool COL>
 inline int launch_batch(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems,
                         int* counter, cudaStream_t s) {
-  if (threads == 256)
+  if (threads == 128)
+    batch_pass_kernel<COL, 128><<<grid, 128, batch_smem<128>(), s>>>(descs, items, nitems, counter);
+  else if (threads == 256)
     batch_pass_kernel<COL, 256><<<grid, 256, batch_smem<256>(), s>>>(descs, items, nitems, counter);
   else
     batch_pass_kernel<COL, 512><<<grid, 512, batch_smem<512>(), s>>>(descs, items, nitems, counter);
@@ -226,7 +297,9 @@ inline int launch_batch(int grid, int threads, const PassDesc* descs, const Batc
 
 template <bool COL>
 inline int prepare_batch() {
-  const bool ok = cudaFuncSetAttribute(batch_pass_kernel<COL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const bool ok = cudaFuncSetAttribute(batch_pass_kernel<COL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_smem<128>()) == cudaSuccess &&
+                  cudaFuncSetAttribute(batch_pass_kernel<COL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)batch_smem<256>()) == cudaSuccess &&
                   cudaFuncSetAttribute(batch_pass_kernel<COL, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)batch_smem<512>()) == cudaSuccess;

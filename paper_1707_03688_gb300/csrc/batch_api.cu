@@ -23,7 +23,7 @@ struct nslct_batch_s {
   // kernels (nslct_forward) instead of the batched launches; chosen by
   // nslct_batch_tune (default: every field batched)
   int split = 1 << 30;
-  int threads = 512;   // CTA size of the batched kernels: 256 when every line is <= 2048
+  int threads = 512;   // CTA size of the batched kernels: 256 when every line is <= 2048 (the tuner may pick 128)
   std::vector<int> Nx, Ny;
   // the fields that run alone are spread over these streams (forked from and
   // joined to the caller's stream by events), so their passes overlap
@@ -97,7 +97,7 @@ void drop_graph(nslct_batch_s* b) {
 // (its counter must be zero).
 int launch_batched_pass(nslct_batch_s* b, int k, cudaStream_t s) {
   if (b->nitems[k] == 0) return NSLCT_OK;
-  const int grid = std::min(b->nitems[k], (b->threads == 256 ? 2 : 1) * b->num_sms);
+  const int grid = std::min(b->nitems[k], (b->threads == 128 ? 3 : b->threads == 256 ? 2 : 1) * b->num_sms);
   const PassDesc* descs = b->d_descs + (size_t)k * b->n;
   const BatchItem* items = b->d_items + b->item_off[k];
   return chain_pass_is_column(k)
@@ -237,6 +237,15 @@ int nslct_batch_set_split(nslct_batch_t b, int split) {
 
 int nslct_batch_get_split(nslct_batch_t b) { return b ? b->split : 0; }
 
+int nslct_batch_set_threads(nslct_batch_t b, int threads) {
+  if (!b || (threads != 128 && threads != 256 && threads != 512)) return NSLCT_E_ARG;
+  for (int f = 0; f < b->n; ++f)
+    if (batch_panel_lines(b->Nx[f], threads) == 0 || batch_panel_lines(b->Ny[f], threads) == 0) return NSLCT_E_SIZE;
+  b->threads = threads;
+  drop_graph(b);
+  return build_items(b);
+}
+
 int nslct_batch_threads(nslct_batch_t b) { return b ? b->threads : 0; }
 
 int nslct_batch_tune(nslct_batch_t b, nslct_stream_t stream, int iters, int* chosen, float* ms_per_forward) {
@@ -256,13 +265,16 @@ int nslct_batch_tune(nslct_batch_t b, nslct_stream_t stream, int iters, int* cho
     if (e0) cudaEventDestroy(e0);
     return NSLCT_E_CUDA;
   }
-  // the batched kernels' CTA size is the other tuned choice: 256 threads (two
-  // CTAs per SM, lines up to 2048) or 512
+  // the batched kernels' CTA size is the other tuned choice: 128 threads
+  // (three CTAs per SM, packed line pairs), 256 (two CTAs per SM) or 512,
+  // each where every field's lines fit it
   std::vector<int> tile = {512};
-  bool fits256 = true;
-  for (int f = 0; f < b->n && fits256; ++f)
-    fits256 = batch_panel_lines(b->Nx[f], 256) != 0 && batch_panel_lines(b->Ny[f], 256) != 0;
-  if (fits256) tile.push_back(256);
+  for (int th : {256, 128}) {
+    bool fits = true;
+    for (int f = 0; f < b->n && fits; ++f)
+      fits = batch_panel_lines(b->Nx[f], th) != 0 && batch_panel_lines(b->Ny[f], th) != 0;
+    if (fits) tile.push_back(th);
+  }
   int best = 1 << 30, best_th = b->threads, rc = NSLCT_OK;
   float best_ms = 0.0f;
   for (int th : tile) {

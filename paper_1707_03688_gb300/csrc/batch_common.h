@@ -11,7 +11,7 @@ struct BatchItem {
 };
 
 // Lines per panel of the batched kernels for line length L with `threads`-thread
-// CTAs (256 or 512; 0 if that CTA size does not handle L).
+// CTAs (128, 256 or 512; 0 if that CTA size does not handle L).
 int batch_panel_lines(int L, int threads);
 
 int launch_batch_row(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,

@@ -3,7 +3,10 @@
 
 namespace nslct {
 int batch_panel_lines(int L, int threads) {
-  return threads == 256 ? batch_lines_of<256>(L) : threads == 512 ? batch_lines_of<512>(L) : 0;
+  return threads == 128   ? batch_lines_of<128>(L)
+         : threads == 256 ? batch_lines_of<256>(L)
+         : threads == 512 ? batch_lines_of<512>(L)
+                          : 0;
 }
 int launch_batch_row(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems, int* counter,
                      cudaStream_t s) {

@@ -1983,7 +1983,9 @@ namespace nslct {
 #ifndef NSLCT_DUAL_X2
 #define NSLCT_DUAL_X2 1
 #endif
-template <int L, int P, int E_>
+// EXACT: every twiddle from the full table (the adjoint); otherwise one base
+// twiddle from the compact table and its powers formed as scalars (batches).
+template <int L, int P, int E_, bool EXACT = true>
 struct LineFftX2 {
   static constexpr int E = E_;
   static constexpr int T_LINE = L / E;
@@ -2016,10 +2018,14 @@ struct LineFftX2 {
       const int j = t + u * T_LINE;
       const int jm = j % NS;
       if constexpr (NS > 1) {
-        float2 w[RD];
-        load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
+        if constexpr (EXACT) {
+          float2 w[RD];
+          load_twiddles<float, RD>(tw + stage_table_offset(L, E, ST) + jm * RD, w);
 #pragma unroll
-        for (int r = 1; r < RD; ++r) x[r] = tw2_apply(x[r], tw2_from(w[r]));
+          for (int r = 1; r < RD; ++r) x[r] = tw2_apply(x[r], tw2_from(w[r]));
+        } else {
+          x2_twiddle_scalar_powers<RD>(x, __ldg(tw + compact_table_offset(L, E, ST) + jm));
+        }
       }
       X2Dft<RD>::run(x, K);
       if constexpr (LAST) {

@@ -51,7 +51,7 @@ EXPORTED = (
     "nslct_plan_theta",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
-    "nslct_batch_threads",
+    "nslct_batch_threads", "nslct_batch_set_threads",
     "nslct_batch_tune", "nslct_batch_forward_pass", "nslct_batch_forward_each", "nslct_batch_destroy",
     "nslct_status", "nslct_selftest_timeout", "nslct_destroy", "nslct_strerror", "nslct_version",
 )
@@ -125,6 +125,7 @@ def load(path: str | None = None):
         "nslct_batch_capture": (ctypes.c_int, [_VP, _VP]),
         "nslct_batch_forward_each": (ctypes.c_int, [_VP, _VP]),
         "nslct_batch_set_split": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "nslct_batch_set_threads": (ctypes.c_int, [_VP, ctypes.c_int]),
         "nslct_batch_get_split": (ctypes.c_int, [_VP]),
         "nslct_batch_threads": (ctypes.c_int, [_VP]),
         "nslct_batch_tune": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -619,13 +620,17 @@ class Batch:
         """Fields with min(Nx, Ny) >= split run through their own fused passes."""
         _check(load().nslct_batch_set_split(_VP(self.handle), int(split)), "nslct_batch_set_split")
 
+    def set_threads(self, threads: int):
+        """Pin the batched kernels' CTA size (128, 256 or 512)."""
+        _check(load().nslct_batch_set_threads(_VP(self.handle), int(threads)), "nslct_batch_set_threads")
+
     @property
     def split(self) -> int:
         return int(load().nslct_batch_get_split(_VP(self.handle)))
 
     @property
     def threads(self) -> int:
-        """CTA size of the batched kernels (256 or 512)."""
+        """CTA size of the batched kernels (128, 256 or 512)."""
         return int(load().nslct_batch_threads(_VP(self.handle)))
 
     def tune(self, stream=None, iters: int = 3):

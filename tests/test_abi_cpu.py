@@ -182,6 +182,7 @@ def test_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.nslct_backward_pass(vp(0), 0, 1, 0, vp(0), vp(0), vp(0), vp(0), vp(0)) == N.NSLCT_E_ARG
     assert lib.nslct_backward_pass(vp(0), 5, 1, 0, vp(0), vp(0), vp(0), vp(0), vp(0)) == N.NSLCT_E_ARG
     assert lib.nslct_batch_forward_pass(vp(0), 0, vp(0)) == N.NSLCT_E_ARG
+    assert lib.nslct_batch_set_threads(vp(0), 128) == N.NSLCT_E_ARG
     # batches: an unsupported size is refused before any plan is made
     nx = (ctypes.c_int * 1)(100)
     ny = (ctypes.c_int * 1)(128)

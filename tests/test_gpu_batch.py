@@ -112,6 +112,44 @@ def test_batch_pass_sequence_equals_forward(N, batch_case):
     assert exc.value.code == N.NSLCT_E_ARG
 
 
+def test_batch_cta_sizes_agree(N, batch_case):
+    """Every batched CTA size, the packed 128-thread one included, gives the
+    single-plan results; graph capture after pinning the size replays them."""
+    b, shapes, abcds, fields, ins, outs = batch_case
+    b.set_split(1 << 30)
+    refs = []
+    for k, (nx, ny) in enumerate(shapes):
+        plan = N.Plan(abcds[k], nx, ny)
+        refs.append(plan.forward(ins[k]).cpu().numpy().astype(np.complex128))
+        plan.close()
+    for th in (128, 256, 512):
+        b.set_threads(th)
+        assert b.threads == th
+        for o in outs:
+            o.zero_()
+        b.forward()
+        torch.cuda.synchronize()
+        for k, (a, o) in enumerate(zip(refs, outs)):
+            assert O.rel_l2(o.cpu().numpy().astype(np.complex128), a) < 2e-6, (th, k, shapes[k])
+    b.set_threads(128)
+    b.forward()
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    s = torch.cuda.Stream()
+    b.capture(s)
+    for o in outs:
+        o.zero_()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        b.forward(stream=s)
+    s.synchronize()
+    for a, o in zip(first, outs):
+        assert torch.equal(a, o)
+    with pytest.raises(N.NslctError) as exc:
+        b.set_threads(64)
+    assert exc.value.code == N.NSLCT_E_ARG
+
+
 def test_batch_rejects_unsupported_sizes(N):
     with pytest.raises(N.NslctError) as exc:
         N.Batch([I.random_symplectic_abcd(1)], [(48, 64)])
@@ -152,7 +190,7 @@ def test_batch_split_and_tune(N, batch_case):
     close_to_ref()
     chosen, ms = b.tune(iters=2)
     sizes = {min(nx, ny) for nx, ny in shapes} | {1 << 30}
-    assert chosen in sizes and b.split == chosen and ms > 0 and b.threads in (256, 512)
+    assert chosen in sizes and b.split == chosen and ms > 0 and b.threads in (128, 256, 512)
     for o in outs:
         o.zero_()
     b.forward()
