@@ -5,8 +5,8 @@
 // same operation sequence. Here the two lines share one 64-bit register pair
 // per quantity: re = (line0.re, line1.re), im = (line0.im, line1.im). One
 // add/sub/mul/fma.f32x2 then does both lines' work. Its lane throughput is
-// that of scalar FP32; what halves is the number of issued instructions, which
-// is what bounds the pair kernel.
+// that of scalar FP32 (a packed instruction holds the FMA pipe for two
+// cycles); what halves is the number of issued instructions.
 //
 // Inverse transforms use J(z) = i conj(z), the swap of the real and imaginary
 // parts: IDFT = J DFT J, and a chirp product commutes with J up to
