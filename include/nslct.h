@@ -348,13 +348,14 @@ int nslct_plan_theta_get(nslct_plan_t plan, double theta[10]);
  *   grad_out, grad_in, grad_theta, grad_chirp   as in nslct_backward.
  *   y_inout    the forward output y (device). It doubles as the value-path
  *              buffer, so on return it holds L^{-1} y, the reconstructed input.
+ *              It must not overlap grad_in (NSLCT_E_ARG).
  * The call makes no allocation of any kind. Its per-CTA partial sums go to a
  * fixed device array inside the library (4 x 2049 x 3 doubles, about 196 KB,
  * enough for every supported size; larger would return NSLCT_E_SIZE), which
  * every GPU that loads the library holds until the process exits. The first
- * call on a device looks that array's device address up (cudaGetSymbolAddress
- * with the plan's device current); make that first call before any stream
- * capture. Each call rewrites all the array entries it reads, so nothing has
+ * call on a device (and the first after the device's context was reset) looks
+ * that array's device address up (cudaGetSymbolAddress with the plan's device
+ * current); make that first call before any stream capture. Each call rewrites all the array entries it reads, so nothing has
  * to be cleared between calls; but every call shares the one array, so calls
  * that overlap on the GPU (other streams, other threads, other plans) race.
  */

@@ -1560,6 +1560,10 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
     if (!s_ok) {
       if (tid == 0) {
         if (d.err) atomicOr(d.err, 1u);
+        // every copy of this panel was issued before the wait: give them one
+        // more bounded wait to land before the shared memory is released,
+        // then drain the stores
+        mbar_wait_bounded(bar, (uint32_t)(it & 1), d.wait_us);
         bulk_wait_all();
       }
       return;

@@ -56,10 +56,9 @@ def test_batch_matches_single_plans_and_oracle(N, batch_case):
         assert O.rel_l2(got, single) < 2e-6, (k, nx, ny)
         # the batch's own plan for this field equals a standalone plan
         np.testing.assert_allclose(b.params(k)["H"], plan.params()["H"], atol=0)
-        if nx * ny <= 256 * 256:
-            params = O.decompose(b.info(k)["abcd"], b.params(k)["H"])
-            ref_o = O.forward(fields[k], params, b.dx[k], b.dy[k])
-            assert O.rel_l2(got, ref_o) < 2e-5, (k, nx, ny)
+        params = O.decompose(b.info(k)["abcd"], b.params(k)["H"])
+        ref_o = O.forward(fields[k], params, b.dx[k], b.dy[k])
+        assert O.rel_l2(got, ref_o) < 2e-5, (k, nx, ny)
         plan.close()
 
 
@@ -148,6 +147,45 @@ def test_batch_cta_sizes_agree(N, batch_case):
     with pytest.raises(N.NslctError) as exc:
         b.set_threads(64)
     assert exc.value.code == N.NSLCT_E_ARG
+
+
+LARGE_SHAPES = [(2048, 2048), (1536, 2048), (2048, 1536), (2048, 128), (128, 2048), (1536, 1536),
+                (1536, 192), (768, 2048), (256, 384), (128, 128)]
+
+
+@pytest.fixture(scope="module")
+def large_case(N):
+    """Fields with the 1536- and 2048-point lines of the 256-field workload,
+    square and not, with their FP64 oracle outputs (computed once)."""
+    abcds = [I.random_symplectic_abcd(3300 + k) for k in range(len(LARGE_SHAPES))]
+    fields = [I.blob_field(nx, ny, seed=3400 + k, width_range=(2.0, max(3.0, min(nx, ny) / 8)))
+              for k, (nx, ny) in enumerate(LARGE_SHAPES)]
+    b = N.Batch(abcds, LARGE_SHAPES)
+    ins = [torch.from_numpy(f).to(torch.complex64).cuda() for f in fields]
+    outs = [torch.empty_like(x) for x in ins]
+    b.bind(ins, outs)
+    refs = []
+    for k in range(len(LARGE_SHAPES)):
+        params = O.decompose(b.info(k)["abcd"], b.params(k)["H"])
+        refs.append(O.forward(fields[k], params, b.dx[k], b.dy[k]))
+    yield b, refs, outs
+    b.close()
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_batch_large_lines_match_oracle(N, large_case, threads):
+    """Every field batched (no per-field passes), at each batched CTA size:
+    each output against the oracle directly, 1536/2048-point lines included."""
+    b, refs, outs = large_case
+    b.set_split(1 << 30)
+    b.set_threads(threads)
+    for o in outs:
+        o.zero_()
+    b.forward()
+    torch.cuda.synchronize()
+    for k, (nx, ny) in enumerate(LARGE_SHAPES):
+        err = O.rel_l2(outs[k].cpu().numpy().astype(np.complex128), refs[k])
+        assert err < 2e-5, (threads, k, nx, ny, err)
 
 
 def test_batch_rejects_unsupported_sizes(N):

@@ -39,7 +39,9 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("nx,ny,precision", [(256, 128, "fp32"), (64, 64, "fp64")])
+# 4096-point lines fill the library's fixed array (2049 rows per pass, 2048 used)
+@pytest.mark.parametrize("nx,ny,precision", [(256, 128, "fp32"), (64, 64, "fp64"), (4096, 64, "fp32"),
+                                             (4096, 4096, "fp32")])
 def test_noalloc_matches_backward_twice(N, nx, ny, precision):
     lib = N.load()
     dt = torch.complex128 if precision == "fp64" else torch.complex64
@@ -81,5 +83,11 @@ def test_noalloc_rejects_bad_arguments(N):
     rc = lib.nslct_backward_noalloc(ctypes.c_void_p(plan.handle), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(0),
                                     ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(0), ctypes.c_void_p(0),
                                     ctypes.c_void_p(0))
+    assert rc == N.NSLCT_E_ARG
+    # grad_in overlapping y_inout (the value path's buffer) is refused
+    y = torch.zeros(64, 64, dtype=torch.complex64, device="cuda")
+    rc = lib.nslct_backward_noalloc(ctypes.c_void_p(plan.handle), ctypes.c_void_p(g.data_ptr()),
+                                    ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(y.data_ptr() + 512),
+                                    ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_void_p(0))
     assert rc == N.NSLCT_E_ARG
     plan.close()
