@@ -54,13 +54,22 @@ PASS_KERNELS = {
     ("fp32", 5): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 2>",
                   "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
     ("fp32", 3): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
-    ("mixed", 5): ["pass_kernel_tma<4096, 0, 1>", "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>",
-                   "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>"],
-    ("mixed", 3): ["pass_kernel_tma<4096, 0, 1>", "pass_kernel_tma<4096, 1, 1>", "pass_kernel_tma<4096, 0, 1>"],
+    ("mixed", 5): ["pass_kernel_tc<false>", "pass_kernel_tc<true>", "pass_kernel_tc<false>", "pass_kernel_tc<true>",
+                   "pass_kernel_tc<false>"],
+    ("mixed", 3): ["pass_kernel_tc<false>", "pass_kernel_tc<true>", "pass_kernel_tc<false>"],
 }
+# tensor-core work of the split-precision kernel per sample and per stage: a
+# data row of R = 64 complex samples (K = 128 real inputs, three FP16 products:
+# K = 384) times the 128-output real-block DFT_R matrix, 2 * 384 * 128 / 64
+# flops; a pass runs two stages per 1D transform
+TC_FLOPS_PER_SAMPLE_STAGE = 2 * 384 * 128 // 64
 # the same for the batched kernel (256 fields {128..2048}^2, all batched; row
 # kernel: mean of passes 1, 3, 5; the 128-thread variant not captured) and
 # the adjoint kernel (64 x 1024^2)
+# the split-precision kernel (set from its own capture; None until then)
+NCU_TRAFFIC_MIXED = {}
+# ncu sm__pipe_tensor_cycles_active (fraction of elapsed cycles) of the split-precision kernel
+TC_PIPE_ACTIVE = {}
 NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 256>": 2.171e9, "batch_pass_kernel<1, 256>": 2.137e9}
 NCU_TRAFFIC_GRAD = {"dual_pass_kernel<float, 1024, 0>": 2.088e9, "dual_pass_kernel<float, 1024, 1>": 2.089e9}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
@@ -230,6 +239,69 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def _measure_step(N, torch, plans, x, outs, stream, steps, warmup, barrier, clocks=None):
+    """Time `steps` steps of the 16 independent transforms (one nslct_forward_group
+    call each), then each pass of every transform with events between passes.
+    Returns (ms per step, mean ms of each pass)."""
+    handles = [p.handle for p in plans]
+    xs = [x] * len(plans)
+
+    def step():
+        N.nslct_forward_group(handles, xs, outs, stream)
+
+    for _ in range(warmup):
+        step()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if clocks is not None:
+        clocks.__enter__()
+    try:
+        barrier()
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    finally:
+        if clocks is not None:
+            clocks.__exit__(None, None, None)
+    ms_step = ev0.elapsed_time(ev1) / steps
+    npass = plans[0].passes()
+    iters = max(1, steps)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(iters * len(plans))]
+    barrier()
+    k = 0
+    for _ in range(iters):
+        for p, o in zip(plans, outs):
+            e = evs[k]
+            e[0].record(stream)
+            for j in range(npass):
+                N.nslct_forward_pass(p.handle, j, x, o, stream)
+                e[j + 1].record(stream)
+            k += 1
+    barrier()
+    pass_ms = np.zeros(npass)
+    for e in evs:
+        for j in range(npass):
+            pass_ms[j] += e[j].elapsed_time(e[j + 1])
+    pass_ms /= len(evs)
+    return ms_step, pass_ms
+
+
+def _roofline_of(precision, npass, pass_ms, traffic):
+    """The dominant kernel's roofline (see _dominant_roofline) and the chain's
+    fraction of the 16 B per sample per pass model."""
+    peak, _ = _peaks()
+    bytes_launch = BYTES_PER_SAMPLE_PASS * NX * NY
+    roof = _dominant_roofline(pass_ms, PASS_KERNELS[(precision, npass)], bytes_launch, traffic)
+    chain_gbs = npass * bytes_launch / (pass_ms.sum() * 1e-3) / 1e9
+    chain = {"pass_ms": [round(float(v), 5) for v in pass_ms], "modelled_bytes_per_sample": npass * BYTES_PER_SAMPLE_PASS,
+             "achieved_gbs": chain_gbs, "frac_of_hbm": chain_gbs / peak,
+             "compulsory_frac": 16 * NX * NY / (pass_ms.sum() * 1e-3) / 1e9 / peak}
+    return roof, chain
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_1707_03688_gb300 import nslct as N
@@ -256,66 +328,14 @@ def run_gpu(args, world, rank, local):
 
     # the transforms of a step are independent: one library call enqueues them
     # alternately on two streams, so one transform's passes fill the last
-    # partial wave of the other's
-    handles = [p.handle for p in plans]
-    xs = [x] * N_ABCD
-
-    def step():
-        N.nslct_forward_group(handles, xs, outs, stream)
-
-    # ---- warm-up
-    for _ in range(args.warmup):
-        step()
-    barrier()
-
-    # ---- timed region (device events on the launching stream)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev.index) as clk:
-        barrier()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-        barrier()
-    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
-    ms_step = ms_total / args.steps
+    # partial wave of the other's. Timed region: device events on the
+    # launching stream, clocks sampled meanwhile.
+    clk = ClockSampler(dev.index)
+    ms_step, pass_ms = _measure_step(N, torch, plans, x, outs, stream, args.steps, args.warmup, barrier, clk)
+    ms_step = max_over_ranks(ms_step, world, dev)
     samples_step = N_ABCD * NX * NY
     value = whole_job_value(samples_step, ms_step, world)
-
-    # ---- per-pass durations (same work, events between the five passes)
-    npass_iters = max(1, args.steps)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(npass_iters * N_ABCD)]
-    barrier()
-    k = 0
-    for _ in range(npass_iters):
-        for p, o in zip(plans, outs):
-            e = evs[k]
-            e[0].record(stream)
-            for j in range(npass):
-                N.nslct_forward_pass(p.handle, j, x, o, stream)
-                e[j + 1].record(stream)
-            k += 1
-    barrier()
-    pass_ms = np.zeros(npass)
-    for e in evs:
-        for j in range(npass):
-            pass_ms[j] += e[j].elapsed_time(e[j + 1])
-    pass_ms /= len(evs)
-    peak, peak_kind = _peaks()
-    bytes_launch = BYTES_PER_SAMPLE_PASS * NX * NY
-    # the dominant kernel: of the kernels that run the passes, the one with the
-    # largest share of the transform's time; its roofline uses its average launch
-    names = PASS_KERNELS[(args.precision, npass)]
-    per_kernel = {}
-    for j, name in enumerate(names):
-        tot, n = per_kernel.get(name, (0.0, 0))
-        per_kernel[name] = (tot + float(pass_ms[j]), n + 1)
-    dom_name = max(per_kernel, key=lambda k: per_kernel[k][0])
-    dom_ms = per_kernel[dom_name][0] / per_kernel[dom_name][1]
-    dom_share = per_kernel[dom_name][0] / float(pass_ms.sum())
-    achieved = bytes_launch / (dom_ms * 1e-3) / 1e9
-    chain_gbs = npass * bytes_launch / (pass_ms.sum() * 1e-3) / 1e9
+    roof, chain = _roofline_of(args.precision, npass, pass_ms, NCU_TRAFFIC)
 
     # ---- end to end: pinned host input -> device -> 16 transforms -> pinned host outputs.
     # Each output's device->host copy runs on a copy stream while the next
@@ -364,18 +384,38 @@ def run_gpu(args, world, rank, local):
                    "streams": "nslct_forward_group: the 16 independent transforms alternate over two CUDA streams",
                    "l2": "no flush: 16 distinct 128 MiB outputs per step, working set 2.1 GB > 126 MB L2"},
         "gpu_launches": args.steps * N_ABCD * npass,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom_name), "kernel": dom_name,
-                     "share": dom_share,
-                     "peak_source": f"hbm_gbs ({peak_kind})",
-                     "bytes_per_launch": bytes_launch, "avg_launch_ms": dom_ms},
-        "chain": {"pass_ms": [round(v, 5) for v in pass_ms], "modelled_bytes_per_sample": npass * BYTES_PER_SAMPLE_PASS,
-                  "achieved_gbs": chain_gbs, "frac_of_hbm": chain_gbs / peak,
-                  "compulsory_frac": 16 * NX * NY / (pass_ms.sum() * 1e-3) / 1e9 / peak},
+        "roofline": roof,
+        "chain": chain,
         "e2e": {"value": e2e_value, "unit": "Msamples/s", "h2d_bytes_per_step": NX * NY * 8,
                 "d2h_bytes_per_step": N_ABCD * NX * NY * 8},
         "clocks": clk.summary(),
     }
+
+    # ---- the split-precision tensor-core form on the same GPU in the same run
+    mixed_outs = None
+    if args.precision == "fp32" and not args.no_mixed:
+        mplans = [N.Plan(m, NX, NY, precision="mixed", method=args.method, decomposition=args.decomposition)
+                  for m in mats]
+        mixed_outs = [torch.empty_like(x) for _ in range(N_ABCD)]
+        mclk = ClockSampler(dev.index)
+        m_ms, m_pass = _measure_step(N, torch, mplans, x, mixed_outs, stream, args.steps, args.warmup, barrier, mclk)
+        m_ms = max_over_ranks(m_ms, world, dev)
+        m_roof, m_chain = _roofline_of("mixed", npass, m_pass, NCU_TRAFFIC_MIXED)
+        # tensor-core work of the dominant kernel per launch: two stages per
+        # 1D transform of the pass program
+        ntr = {"pass_kernel_tc<true>": 2}.get(m_roof["kernel"], 2)
+        m_flops = TC_FLOPS_PER_SAMPLE_STAGE * 2 * ntr * NX * NY
+        result["mixed"] = {
+            "value": whole_job_value(samples_step, m_ms, world), "unit": "Msamples/s", "ms_per_step": m_ms,
+            "dtype": "f16-split+f32",
+            "vs_fp32": (whole_job_value(samples_step, m_ms, world) / value) if value else None,
+            "roofline": m_roof, "chain": m_chain,
+            "tensor": {"flops_per_launch": m_flops, "achieved_tflops": m_flops / (m_roof["avg_launch_ms"] * 1e-3) / 1e12,
+                       "pipe_tensor_active": TC_PIPE_ACTIVE.get(m_roof["kernel"])},
+            "clocks": mclk.summary(),
+        }
+        for p in mplans:
+            p.close()
 
     # ---- CPU baseline and rel-L2: the oracle on one 4096^2 transform (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -394,6 +434,12 @@ def run_gpu(args, world, rank, local):
         gpu_out = outs[0].cpu().numpy().astype(np.complex128)
         result["rel_l2"] = {f"{args.precision}_vs_oracle": O.rel_l2(gpu_out, ref), "field": "ABCD seed 200, 4096^2",
                             "tolerance": 2e-5 if args.precision == "fp32" else 1e-4}
+        if mixed_outs is not None:
+            # both precisions plan ABCD seed 200 with the same H (the same search)
+            err = O.rel_l2(mixed_outs[0].cpu().numpy().astype(np.complex128), ref)
+            result["rel_l2"]["mixed_vs_oracle"] = err
+            result["mixed"]["rel_l2_vs_oracle"] = err
+            result["mixed"]["tolerance"] = 1e-4
         result["cpu_baseline"] = {"value": NX * NY / t_cpu / 1e6, "unit": "Msamples/s", "cores": _blas_threads(),
                                   "kind": "oracle",
                                   "sample": "one 4096x4096 forward transform (ABCD seed 200), FP64 dense DFT-matrix sums",
@@ -652,6 +698,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="leave out the split-precision form that the default line reports beside FP32")
     ap.add_argument("--workload", default="fp32", choices=["fp32", "batch", "grad", "filter"],
                     help="fp32: 4096^2 x 16 ABCD (the benchmark line); batch: 256 uneven fields; "
                          "grad: 64 x 1024^2 forward + backward; filter: two-domain filtering, Eqs. Add04/Add08")
@@ -660,7 +708,8 @@ def main():
     ap.add_argument("--decomposition", default="type1", choices=["type1", "type2", "trace"],
                     help="CM-CC-CM-CC (Eq. HA28), CC-CM-CC-CM (Eq. CCCMCCCM16) or the tr(B) rule (Eq. Reversible08)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
-                    help="fp32: FP32 FFT arithmetic; mixed: radix-16 stages as split-FP16 tensor-core DFT-16")
+                    help="fp32: FP32 FFT arithmetic; mixed: 4096-point lines as four-step DFT-64 stages on the "
+                         "tensor cores (split FP16, FP32 accumulation)")
     ap.add_argument("--n-abcd", type=int, default=16,
                     help="ABCD matrices per step (16 is the benchmark workload; fewer only for profiling captures)")
     args = ap.parse_args()

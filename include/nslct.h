@@ -91,11 +91,14 @@ typedef struct CUstream_st* nslct_stream_t;  /* same type as cudaStream_t */
 /* Arithmetic of the transform. */
 #define NSLCT_PREC_FP32     0x000u /* complex64 data, FP32 FFT arithmetic (default) */
 #define NSLCT_PREC_FP64     0x100u /* complex128 data, FP64 arithmetic throughout */
-/* complex64 data; the radix-16 FFT stages of 256..4096-point lines run as
- * DFT-16 products on the tensor cores with operands split into FP16 halves
- * (x = x_hi + x_lo, W = W_hi + W_lo; x_hi W_hi + x_hi W_lo + x_lo W_hi,
- * FP32 accumulation); every other step stays FP32. Backward and batched
- * calls of such a plan run in FP32. */
+/* complex64 data; the 1D DFTs of 4096-point lines run as two DFT-64 stages
+ * (four-step) on the fifth-generation tensor cores (tcgen05, FP32
+ * accumulators in tensor memory), those of 256..2048-point lines as
+ * radix-16 DFT-16 products on the warp-level tensor cores; operands are split
+ * into FP16 halves (x = x_hi + x_lo, W = W_hi + W_lo;
+ * x_lo W_hi + x_hi W_lo + x_hi W_hi, FP32 accumulation) after exact
+ * power-of-two scaling. Twiddles, chirps and scales stay FP32. Backward and
+ * uneven-batch (nslct_plan_batch) calls of such a plan run in FP32. */
 #define NSLCT_PREC_SPLIT_F16 0x200u
 #define NSLCT_PREC_MASK     0xF00u
 
@@ -335,6 +338,23 @@ int nslct_backward_pass(nslct_plan_t plan, int pass, int nbatch, long long strid
  */
 int nslct_plan_theta(nslct_plan_t* out, const double theta[10], const double h0[4], int Nx, int Ny,
                      double dx, double dy, unsigned flags);
+
+/*
+ * nslct_plan_theta_set -- move a plan made by nslct_plan_theta with an h0 to
+ * new parameters theta (10 doubles, as there), with H(theta) from the same h0:
+ * the plan then equals nslct_plan_theta(theta, h0) of the same size, spacings
+ * and flags. The derivation of Eqs. Intro12 and Bnonsym08 (M, H, B', C1, C2,
+ * the Q0.64 chirp coefficients and the theta Jacobian) runs in FP64 on the
+ * host; nothing is allocated and no CUDA call is made, so it may be called
+ * between the steps of an optimisation loop at no device cost.
+ * Transforms already enqueued keep the parameters they were enqueued with
+ * (the chirps are kernel arguments); enqueueing on the plan from another
+ * thread during the call is not allowed. NSLCT_E_UNSUPPORTED for plans not
+ * made that way (h0 NULL, padded, type 2); NSLCT_E_ARG if L is singular or
+ * theta not finite; NSLCT_E_INFEASIBLE if B' is singular at theta. On error
+ * the plan is unchanged.
+ */
+int nslct_plan_theta_set(nslct_plan_t plan, const double theta[10]);
 
 /* nslct_plan_theta_get -- theta of the plan's ABCD (NSLCT_E_UNSUPPORTED if A is singular). */
 int nslct_plan_theta_get(nslct_plan_t plan, double theta[10]);

@@ -72,6 +72,7 @@ void free_plan(nslct_plan_s* p) {
   if (p->pad_ws) cudaFree(p->pad_ws);
   if (p->err) cudaFree(p->err);
   if (p->partials) cudaFree(p->partials);
+  if (p->tc_tab) cudaFree(p->tc_tab);
   // the four twiddle pointers may alias each other: free each table once
   void* tabs[4] = {p->tw_x, p->tw_y, p->tw16_x, p->tw16_y};
   for (int i = 0; i < 4; ++i) {
@@ -83,6 +84,11 @@ void free_plan(nslct_plan_s* p) {
 }
 
 int launch(const nslct_plan_s* p, bool col, const PassDesc& d, cudaStream_t s) {
+  if (p->mixed && p->tc_tab) {
+    // split-precision plans: the tensor-core kernel where it runs the pass
+    const int rc = launch_pass_tc(col, d, s);
+    if (rc != NSLCT_E_UNSUPPORTED) return rc;
+  }
   if (d.nbatch > 1 && !(p->prec == 0 && !p->mixed && pair_kernel_length(col ? d.Nx : d.Ny))) {
     // a kernel without a batch dimension: one launch per field
     const size_t esz = p->prec == 1 ? 16 : 8;
@@ -211,6 +217,7 @@ void build_chain_descs(const nslct_plan_s* p, const void* in, void* out, bool in
     d[k].num_sms = p->num_sms;
     d[k].err = p->err;
     d[k].mixed = p->mixed;
+    d[k].tc_tab = p->tc_tab;
   }
 }
 
@@ -367,6 +374,28 @@ static int derive_type1(const double m[16], unsigned flags, const double* h_user
   return NSLCT_OK;
 }
 
+// The host fields of a plan that follow from its (validated) ABCD and
+// decomposition: flags, M, H, B', C1, C2, the Q0.64 chirps, the three-pass
+// choice and theta with its chirp Jacobian. Touches no device.
+static void set_derived(nslct_plan_s* p, const double m[16], const Decomp& dc, int type2, unsigned flags) {
+  p->type2 = type2;
+  p->flags = (flags & ~NSLCT_TYPE2) | (type2 ? NSLCT_TYPE2 : 0u);
+  std::memcpy(p->M, m, 16 * sizeof(double));
+  const Mat2* src[4] = {&dc.H, &dc.Bp, &dc.C1, &dc.C2};
+  double* dst[4] = {p->H, p->Bp, p->C1, p->C2};
+  for (int k = 0; k < 4; ++k) {
+    dst[k][0] = src[k]->m00; dst[k][1] = src[k]->m01; dst[k][2] = src[k]->m10; dst[k][3] = src[k]->m11;
+  }
+  fill_chirps(p);
+  p->y_only_h = (p->prec == 0 && !(flags & NSLCT_FULL_CHAIN) && p->H[0] == 0.0 && p->H[1] == 0.0 && p->H[2] == 0.0)
+                    ? 1 : 0;
+  // theta gradients follow the type-1 chain of M only
+  p->has_theta = (!p->type2 && theta_from_abcd(p->M, p->theta)) ? 1 : 0;
+  // the Jacobian of the H(theta) rule about its anchor (the plan's own H
+  // when it was not made from an anchor h0)
+  if (p->has_theta) chirp_jacobian(p->theta, p->has_h0 ? p->h0 : p->H, p->jac);
+}
+
 int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, double dx, double dy,
                   unsigned flags, const double* h_user) {
   if (!out) return NSLCT_E_ARG;
@@ -386,22 +415,9 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   nslct_plan_s* p = new (std::nothrow) nslct_plan_s();
   if (!p) return NSLCT_E_NOMEM;
   p->Nx = Nx; p->Ny = Ny; p->dx = dx; p->dy = dy;
-  p->type2 = type2;
-  p->flags = (flags & ~NSLCT_TYPE2) | (type2 ? NSLCT_TYPE2 : 0u);
   p->prec = prec_flag == NSLCT_PREC_FP64 ? 1 : 0;
   p->mixed = prec_flag == NSLCT_PREC_SPLIT_F16 ? 1 : 0;
-  std::memcpy(p->M, m, sizeof(m));
-  const Mat2* src[4] = {&dc.H, &dc.Bp, &dc.C1, &dc.C2};
-  double* dst[4] = {p->H, p->Bp, p->C1, p->C2};
-  for (int k = 0; k < 4; ++k) {
-    dst[k][0] = src[k]->m00; dst[k][1] = src[k]->m01; dst[k][2] = src[k]->m10; dst[k][3] = src[k]->m11;
-  }
-  fill_chirps(p);
-  p->y_only_h = (p->prec == 0 && !(flags & NSLCT_FULL_CHAIN) && p->H[0] == 0.0 && p->H[1] == 0.0 && p->H[2] == 0.0)
-                    ? 1 : 0;
-  // theta gradients follow the type-1 chain of M only
-  p->has_theta = (!p->type2 && theta_from_abcd(p->M, p->theta)) ? 1 : 0;
-  if (p->has_theta) chirp_jacobian(p->theta, p->H, p->jac);
+  set_derived(p, m, dc, type2, flags);
 
   if (cudaGetDevice(&p->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
@@ -433,6 +449,19 @@ int nslct_plan_ex(nslct_plan_t* out, const double abcd[16], int Nx, int Ny, doub
   }
   if (rc == NSLCT_OK) rc = p->prec ? prepare_pass_f64(Nx) : prepare_pass_f32(Nx);
   if (rc == NSLCT_OK && Ny != Nx) rc = p->prec ? prepare_pass_f64(Ny) : prepare_pass_f32(Ny);
+  if (rc == NSLCT_OK && p->mixed && (tc_length(Nx) || tc_length(Ny))) {
+    // the tensor-core kernel's constants (DFT matrix halves and twiddles)
+    std::vector<unsigned char> tab(tc_table_bytes(), 0);
+    tc_build_table(tab.data());
+    if (cudaMalloc(&p->tc_tab, tab.size()) != cudaSuccess) {
+      p->tc_tab = nullptr;
+      rc = NSLCT_E_NOMEM;
+    } else if (cudaMemcpy(p->tc_tab, tab.data(), tab.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = NSLCT_E_CUDA;
+    } else {
+      rc = prepare_pass_tc();
+    }
+  }
   if (rc != NSLCT_OK) { free_plan(p); return rc; }
   *out = p;
   return NSLCT_OK;
@@ -478,7 +507,33 @@ int nslct_plan_theta(nslct_plan_t* out, const double theta[10], const double h0[
     if (!std::isfinite(h0[i])) return NSLCT_E_ARG;
   double h[4];
   h_of_theta(theta, h0, h);
-  return nslct_plan_ex(out, m, Nx, Ny, dx, dy, flags | NSLCT_H_USER, h);
+  const int rc = nslct_plan_ex(out, m, Nx, Ny, dx, dy, flags | NSLCT_H_USER, h);
+  if (rc == NSLCT_OK) {
+    nslct_plan_s* p = *out;
+    std::memcpy(p->h0, h0, sizeof(p->h0));
+    p->has_h0 = 1;
+    if (p->has_theta) chirp_jacobian(p->theta, p->h0, p->jac);
+  }
+  return rc;
+}
+
+int nslct_plan_theta_set(nslct_plan_t p, const double theta[10]) {
+  if (!p || !theta) return NSLCT_E_ARG;
+  if (!p->has_h0 || p->padded || p->type2) return NSLCT_E_UNSUPPORTED;
+  for (int i = 0; i < 10; ++i)
+    if (!std::isfinite(theta[i])) return NSLCT_E_ARG;
+  const double det_l = theta[3] * theta[6] - theta[4] * theta[5];
+  if (!(std::fabs(det_l) > 1e-12)) return NSLCT_E_ARG;
+  double m[16], h[4], mm[16];
+  abcd_from_theta(theta, m);
+  h_of_theta(theta, p->h0, h);
+  const unsigned flags = (p->flags & ~(unsigned)(NSLCT_H_MASK | NSLCT_PROJECT_SP4 | NSLCT_TYPE2)) | NSLCT_H_USER;
+  Decomp dc{};
+  int type2 = 0;
+  const int rc = derive(m, flags, h, mm, &dc, &type2);
+  if (rc != NSLCT_OK) return rc;  // the plan is left as it was
+  set_derived(p, mm, dc, type2, flags);
+  return NSLCT_OK;
 }
 
 int nslct_plan_theta_get(nslct_plan_t p, double theta[10]) {

@@ -91,6 +91,11 @@ struct PassDesc {
   unsigned int test_extra_tx;
   // the same pass as a program for the packed line-pair kernel (set by its launcher)
   X2Prog x2;
+  // split-precision tensor-core kernel: its constant operands (DFT matrix
+  // halves and twiddles, see tc_pass.cu) and whether the program's first
+  // transform is an inverse (set by its launcher)
+  const void* tc_tab;
+  int x2_first_inv;
 };
 
 // FP32 lines of 256..4096 points run in the line-pair kernel (which also
@@ -127,6 +132,16 @@ int build_schedule(const nslct_plan_s* p, const void* in, void* out, bool invers
 // True when L is a length the kernels are instantiated for.
 bool supported_length(int L);
 
+// Split-precision passes on the tensor cores (tc_pass.cu): the line lengths
+// the kernel runs, the size of its constant table and the table's bytes,
+// kernel attributes, and one pass (NSLCT_E_UNSUPPORTED when the pass is not
+// one it runs: the caller then uses the FP32 kernels).
+bool tc_length(int L);
+size_t tc_table_bytes();
+void tc_build_table(unsigned char* host);
+int prepare_pass_tc();
+int launch_pass_tc(bool col, const PassDesc& d, cudaStream_t s);
+
 }  // namespace nslct
 
 struct nslct_plan_s;
@@ -151,6 +166,8 @@ struct nslct_plan_s {
   int num_sms;         // multiprocessors of `device`
   int has_theta;       // A invertible: theta and its chirp Jacobian are defined
   double theta[10];    // (c11,c12,c22, l11,l12,l21,l22, b11,b12,b22), see grad_math.cpp
+  int has_h0;          // made by nslct_plan_theta with an H anchor: nslct_plan_theta_set applies
+  double h0[4];        // that anchor of the H(theta) rule
   double jac[120];     // d(H, B', C1, C2 entries)/d theta, 12 x 10
   void* ws;            // backward value-path field(s) (made on first use, grown for batches)
   long long ws_elems;  // elements `ws` holds
@@ -161,6 +178,7 @@ struct nslct_plan_s {
   void* tw_y;          // device twiddles for length Ny (tables may alias each other)
   void* tw16_x;        // twiddles for elems_per_thread(Nx): adjoint and batched kernels
   void* tw16_y;
+  void* tc_tab;        // split-precision plans with a 4096-point axis: tensor-core kernel constants
   // zero padding: the caller's input field is the in_rows x in_cols region at
   // (in_r0, in_c0) of the Nx x Ny grid the chain runs on; the output is the
   // out_* region (the whole grid unless cropped). pad_ws holds the tiled grid

@@ -48,7 +48,7 @@ EXPORTED = (
     "nslct_inverse_many",
     "nslct_backward_many", "nslct_backward_pass", "nslct_plan_passes", "nslct_forward_pass", "nslct_backward",
     "nslct_backward_noalloc",
-    "nslct_plan_theta",
+    "nslct_plan_theta", "nslct_plan_theta_set",
     "nslct_plan_theta_get", "nslct_plan_batch", "nslct_batch_size", "nslct_batch_plan", "nslct_batch_bind",
     "nslct_batch_forward", "nslct_batch_capture", "nslct_batch_set_split", "nslct_batch_get_split",
     "nslct_batch_threads", "nslct_batch_set_threads",
@@ -116,6 +116,7 @@ def load(path: str | None = None):
         "nslct_plan_theta": (ctypes.c_int, [ctypes.POINTER(_VP), _PD, _PD, ctypes.c_int, ctypes.c_int, _D, _D,
                                             ctypes.c_uint]),
         "nslct_plan_theta_get": (ctypes.c_int, [_VP, _PD]),
+        "nslct_plan_theta_set": (ctypes.c_int, [_VP, _PD]),
         "nslct_plan_batch": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _PD, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int), _PD, _PD, ctypes.c_uint]),
         "nslct_batch_size": (ctypes.c_int, [_VP]),
@@ -369,6 +370,12 @@ def nslct_plan_theta(theta, nx: int, ny: int, dx: float, dy: float, h0=None, fla
     return handle.value
 
 
+def nslct_plan_theta_set(plan: int, theta):
+    """Move a theta plan (made with h0) to new parameters: host FP64 only."""
+    _th, pth = _dbl(theta, 10)
+    _check(load().nslct_plan_theta_set(_VP(plan), pth), "nslct_plan_theta_set")
+
+
 def nslct_plan_theta_get(plan: int):
     th, pth = _out(10)
     _check(load().nslct_plan_theta_get(_VP(plan), pth), "nslct_plan_theta_get")
@@ -468,6 +475,10 @@ class Plan:
 
     def theta(self):
         return nslct_plan_theta_get(self.handle)
+
+    def set_theta(self, theta):
+        """Move a plan made by from_theta with h0 to new parameters (no allocation, no CUDA call)."""
+        nslct_plan_theta_set(self.handle, theta)
 
     def backward(self, grad_out, y, grad_in=None, want_theta=True, want_chirp=False, workspace=None, stream=None):
         """Returns (grad_in, grad_theta or None, grad_chirp or None); gradients are device float64 tensors.

@@ -138,6 +138,71 @@ def test_autograd_function(N):
     assert _rel(th.grad.cpu().numpy(), ogth) < 1e-9
 
 
+def test_theta_set_equals_a_fresh_theta_plan(N):
+    """nslct_plan_theta_set moves a plan to new parameters exactly as
+    nslct_plan_theta would plan them (same H rule anchor): the same
+    decomposition, the same outputs bit for bit and the same gradients."""
+    nx, ny = 128, 96
+    m, h0, x, yt = _case(nx, ny, 21)
+    th1 = O.theta_from_abcd(m)
+    th2 = th1 + np.random.default_rng(5).normal(0.0, 0.05, 10)
+    moved = N.Plan.from_theta(th1, nx, ny, h0=h0)
+    moved.set_theta(th2)
+    fresh = N.Plan.from_theta(th2, nx, ny, h0=h0)
+    for k in ("H", "Bp", "C1", "C2"):
+        np.testing.assert_array_equal(moved.params()[k], fresh.params()[k])
+    np.testing.assert_array_equal(moved.theta(), fresh.theta())
+    xd = torch.from_numpy(x).to(torch.complex64).cuda()
+    ya, yb = moved.forward(xd), fresh.forward(xd)
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yb)
+    gy = 2 * (ya - torch.from_numpy(yt).to(torch.complex64).cuda())
+    ga, tha, _ = moved.backward(gy, ya)
+    gb, thb, _ = fresh.backward(gy, yb)
+    torch.cuda.synchronize()
+    assert torch.equal(ga, gb) and torch.equal(tha, thb)
+    # a plan without an H anchor cannot be moved; a failed move leaves the plan as it was
+    plain = N.Plan(m, nx, ny)
+    with pytest.raises(N.NslctError) as exc:
+        plain.set_theta(th2)
+    assert exc.value.code == N.NSLCT_E_UNSUPPORTED
+    bad = th2.copy()
+    bad[3:7] = 0.0  # singular L
+    with pytest.raises(N.NslctError) as exc:
+        moved.set_theta(bad)
+    assert exc.value.code == N.NSLCT_E_ARG
+    np.testing.assert_array_equal(moved.params()["H"], fresh.params()["H"])
+    for p in (moved, fresh, plain):
+        p.close()
+
+
+def test_autograd_reuses_one_plan_across_theta(N):
+    """With an anchor h0 the autograd function keeps one plan and moves it to
+    each call's theta; two forwards then two backwards (the plan moved between
+    a forward and its backward) give the oracle's gradients for each call."""
+    from paper_1707_03688_gb300 import autograd as A
+    nx = ny = 64
+    m, h0, x, yt = _case(nx, ny, 31)
+    th0 = O.theta_from_abcd(m)
+    ths = [th0, th0 + np.random.default_rng(6).normal(0.0, 0.03, 10)]
+    xs, losses = [], []
+    for th in ths:
+        tht = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+        xd = torch.from_numpy(x).to(torch.complex128).cuda().requires_grad_(True)
+        y = A.nslct_transform(xd, tht, torch.from_numpy(h0), precision="fp64")
+        losses.append(torch.sum(torch.abs(y - torch.from_numpy(yt).cuda()) ** 2))
+        xs.append((xd, tht))
+    key_h0 = np.ascontiguousarray(h0, dtype=np.float64).reshape(4).tobytes()
+    n_cached = sum(1 for k in A._PLANS if k[1:4] == (nx, ny, "fp64") and k[4] == key_h0)
+    assert n_cached == 1
+    for (xd, tht), loss, th in zip(xs, losses, ths):
+        loss.backward()
+        _, ogx, ogth, _ = O.loss_and_grad(x, yt, O.abcd_from_theta(th), h0, I.default_spacing(nx),
+                                          I.default_spacing(ny))
+        assert _rel(xd.grad.cpu().numpy(), ogx) < 1e-11
+        assert _rel(tht.grad.cpu().numpy(), ogth) < 1e-9
+
+
 def test_backward_rejects_misaligned_and_singular_a(N):
     # A = 0 (the 2D DFT): theta is undefined, so only the chirp gradients exist
     z, e = np.zeros((2, 2)), np.eye(2)

@@ -1,6 +1,7 @@
-"""Split-precision mode (NSLCT_PREC_SPLIT_F16): radix-16 stages as FP16 hi/lo
-tensor-core DFT-16 products with FP32 accumulation. Parity bound: relative L2
-<= 1e-4 against the FP64 oracle."""
+"""Split-precision mode (NSLCT_PREC_SPLIT_F16): 4096-point lines as four-step
+DFT-64 stages on the tcgen05 tensor cores (FP16 hi/lo operands, FP32
+accumulation in TMEM); the other lengths as FP16 hi/lo DFT-16 products.
+Parity bound: relative L2 <= 1e-4 against the FP64 oracle."""
 from __future__ import annotations
 
 import numpy as np
@@ -78,3 +79,39 @@ def test_mixed_subnormal_and_extreme_inputs(N):
     out = _run(plan, g.astype(np.complex128))
     assert np.all(np.isfinite(out))
     assert O.rel_l2(out, _oracle(plan, g.astype(np.complex128))) < TOL_MIXED
+
+
+@pytest.mark.parametrize("nx,ny,method", [(4096, 768, "ha"), (768, 4096, "ha"), (512, 4096, "lc_y")])
+def test_mixed_tcgen05_lines_match_oracle(N, nx, ny, method):
+    """The tensor-core kernel's tile schedule: 384 tiles over 152 CTAs (pairs of
+    tiles and a lone last tile per CTA) along either axis, and the three-pass
+    schedule whose row pass runs three 4096-point transforms; forward, inverse
+    and reversibility against the oracle, with no expired wait."""
+    m = I.random_symplectic_abcd(nx + 7 * ny)
+    g = I.blob_field(nx, ny, seed=nx + 3 * ny, width_range=(2.0, 24.0))
+    plan = N.Plan(m, nx, ny, precision="mixed", method=method)
+    if method == "lc_y":
+        assert plan.passes() == 3
+    out = _run(plan, g)
+    assert O.rel_l2(out, _oracle(plan, g)) < TOL_MIXED
+    inv = _run(plan, g, inverse=True)
+    assert O.rel_l2(inv, _oracle(plan, g, inverse=True)) < TOL_MIXED
+    assert O.rel_l2(_run(plan, out, inverse=True), g) < TOL_MIXED
+    assert N.nslct_status(plan.handle) == N.NSLCT_OK
+    plan.close()
+
+
+def test_mixed_tcgen05_batch_equals_single(N):
+    """A same-plan batch runs its 4096-point row passes as one tensor-core
+    launch over all fields; each field equals its own transform bit for bit."""
+    nx, ny, nb = 256, 4096, 3
+    plan = N.Plan(I.random_symplectic_abcd(77), nx, ny, precision="mixed")
+    xs = torch.stack([torch.from_numpy(I.blob_field(nx, ny, seed=80 + b)).to(torch.complex64) for b in range(nb)]).cuda()
+    ys = torch.empty_like(xs)
+    N.nslct_forward_many(plan.handle, xs, ys)
+    torch.cuda.synchronize()
+    for b in range(nb):
+        yb = plan.forward(xs[b].contiguous())
+        torch.cuda.synchronize()
+        assert torch.equal(yb, ys[b])
+    plan.close()
