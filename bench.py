@@ -54,9 +54,9 @@ PASS_KERNELS = {
     ("fp32", 5): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 2>",
                   "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
     ("fp32", 3): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
-    ("mixed", 5): ["pass_kernel_tc<false>", "pass_kernel_tc<true>", "pass_kernel_tc<false>", "pass_kernel_tc<true>",
-                   "pass_kernel_tc<false>"],
-    ("mixed", 3): ["pass_kernel_tc<false>", "pass_kernel_tc<true>", "pass_kernel_tc<false>"],
+    ("mixed", 5): ["pass_kernel_tc<0>", "pass_kernel_tc<1>", "pass_kernel_tc<0>", "pass_kernel_tc<1>",
+                   "pass_kernel_tc<0>"],
+    ("mixed", 3): ["pass_kernel_tc<0>", "pass_kernel_tc<1>", "pass_kernel_tc<0>"],
 }
 # tensor-core work of the split-precision kernel per sample and per stage: a
 # data row of R = 64 complex samples (K = 128 real inputs, three FP16 products:
@@ -66,10 +66,11 @@ TC_FLOPS_PER_SAMPLE_STAGE = 2 * 384 * 128 // 64
 # the same for the batched kernel (256 fields {128..2048}^2, all batched; row
 # kernel: mean of passes 1, 3, 5; the 128-thread variant not captured) and
 # the adjoint kernel (64 x 1024^2)
-# the split-precision kernel (set from its own capture; None until then)
-NCU_TRAFFIC_MIXED = {}
-# ncu sm__pipe_tensor_cycles_active (fraction of elapsed cycles) of the split-precision kernel
-TC_PIPE_ACTIVE = {}
+# the split-precision tcgen05 kernel (one capture of passes 1-3 of a forward,
+# profiles/pass_kernel_tc_4096x4096_ncu.md; rows: mean of passes 1 and 3)
+NCU_TRAFFIC_MIXED = {"pass_kernel_tc<1>": 214.6e6, "pass_kernel_tc<0>": 212.8e6}
+# ncu sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed / 100, same capture
+TC_PIPE_ACTIVE = {"pass_kernel_tc<1>": 0.195, "pass_kernel_tc<0>": 0.238}
 NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 256>": 2.171e9, "batch_pass_kernel<1, 256>": 2.137e9}
 NCU_TRAFFIC_GRAD = {"dual_pass_kernel<float, 1024, 0>": 2.088e9, "dual_pass_kernel<float, 1024, 1>": 2.089e9}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
@@ -402,9 +403,12 @@ def run_gpu(args, world, rank, local):
         m_ms = max_over_ranks(m_ms, world, dev)
         m_roof, m_chain = _roofline_of("mixed", npass, m_pass, NCU_TRAFFIC_MIXED)
         # tensor-core work of the dominant kernel per launch: two stages per
-        # 1D transform of the pass program
-        ntr = {"pass_kernel_tc<true>": 2}.get(m_roof["kernel"], 2)
-        m_flops = TC_FLOPS_PER_SAMPLE_STAGE * 2 * ntr * NX * NY
+        # 1D transform of its passes (five-pass chain: 1, 2, 2, 2, 1 transforms;
+        # three-pass chain: 3, 2, 1), averaged over the passes it runs
+        ntrs = [1, 2, 2, 2, 1] if npass == 5 else [3, 2, 1]
+        names = PASS_KERNELS[("mixed", npass)]
+        dom = [t for t, nm in zip(ntrs, names) if nm == m_roof["kernel"]]
+        m_flops = TC_FLOPS_PER_SAMPLE_STAGE * 2 * (sum(dom) / len(dom)) * NX * NY
         result["mixed"] = {
             "value": whole_job_value(samples_step, m_ms, world), "unit": "Msamples/s", "ms_per_step": m_ms,
             "dtype": "f16-split+f32",
@@ -668,6 +672,23 @@ def run_grad_workload(args, world, rank):
     ms_fwd = _timed(lambda: N.nslct_forward_many(plan.handle, x, y, stream), args.steps, args.warmup, stream)
     pass_ms = _pass_times(lambda k: N.nslct_backward_pass(plan.handle, k, gy, y, gx, ws, stream), 5,
                           max(1, args.steps // 5), stream)
+    # moving the parameters between optimisation steps: a fresh theta plan
+    # (FP64 host derivation, device tables and workspace allocated and uploaded)
+    # against nslct_plan_theta_set on one plan (the same host derivation only)
+    h0 = plan.params()["H"]
+    reps = 20
+    t0 = time.perf_counter()
+    for k in range(reps):
+        pk = N.Plan.from_theta(theta + 1e-4 * k, n, n, h0=h0)
+        pk.close()
+    torch.cuda.synchronize()
+    replan_ms = (time.perf_counter() - t0) * 1e3 / reps
+    moved = N.Plan.from_theta(theta, n, n, h0=h0)
+    t0 = time.perf_counter()
+    for k in range(reps * 50):
+        moved.set_theta(theta + 1e-6 * (k % 7))
+    set_us = (time.perf_counter() - t0) * 1e6 / (reps * 50)
+    moved.close()
     # each dual pass reads and writes two complex64 fields (gradient and value paths)
     roof = _dominant_roofline(pass_ms, [f"dual_pass_kernel<float, {n}, {c}>" for c in (0, 1, 0, 1, 0)],
                               2 * BYTES_PER_SAMPLE_PASS * nb * n * n, NCU_TRAFFIC_GRAD)
@@ -684,6 +705,8 @@ def run_grad_workload(args, world, rank):
         # share: of the whole step (forward, residual, backward, finalisation)
         "roofline": roof,
         "forward_ms": ms_fwd, "backward_pass_ms": [round(float(v), 5) for v in pass_ms],
+        "theta_update": {"fresh_plan_ms": replan_ms, "plan_theta_set_us": set_us,
+                         "note": "host time per parameter update; the step itself does neither"},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
