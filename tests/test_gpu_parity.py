@@ -281,11 +281,12 @@ def test_fp64_4096_full_oracle(N, field_4096):
     assert O.rel_l2(out, ref) < tol64(4096, 4096)
 
 
-def test_bounded_wait_expires_and_plan_recovers(N):
+@pytest.mark.parametrize("n", [256, 4096])
+def test_bounded_wait_expires_and_plan_recovers(N, n):
     """Failure detection without a fault: a pass whose barriers can never
     complete gives up after 1 ms in every CTA, the plan's status word reports
-    it once, and the plan (and context) keep working."""
-    n = 256
+    it once, and the plan (and context) keep working (256: the line-pair
+    kernel; 4096: its three-buffer ring variant)."""
     plan = _plan(N, I.random_symplectic_abcd(1), n, n)
     g = I.blob_field(n, n, seed=1)
     x = torch.from_numpy(g).to(torch.complex64).cuda()
