@@ -521,6 +521,10 @@ def run_batch_workload(args, world, rank):
     with torch.cuda.stream(stream):
         ms_each = _timed(lambda: b.forward_each(stream), args.steps, args.warmup, stream)
         b.set_split(1 << 30)
+        if args.batch_threads:
+            # pinned CTA size (for profiling captures of one variant): the first
+            # batched launches of the run use it
+            b.set_threads(args.batch_threads)
         ms_all_batched = _timed(lambda: b.forward(stream), args.steps, args.warmup, stream)
         split, _ = b.tune(stream, iters=2)
         # the tuned CTA size with every field batched: each pass is one
@@ -733,6 +737,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
                     help="fp32: FP32 FFT arithmetic; mixed: 4096-point lines as four-step DFT-64 stages on the "
                          "tensor cores (split FP16, FP32 accumulation)")
+    ap.add_argument("--batch-threads", type=int, default=0, choices=[0, 128, 256, 512],
+                    help="--workload batch: CTA size of the first all-batched launches (0: the library default)")
     ap.add_argument("--n-abcd", type=int, default=16,
                     help="ABCD matrices per step (16 is the benchmark workload; fewer only for profiling captures)")
     args = ap.parse_args()

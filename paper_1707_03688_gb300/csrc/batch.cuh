@@ -200,19 +200,85 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
   }
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   ulonglong2* xs2 = reinterpret_cast<ulonglong2*>(xs);
-  if (d.t1 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t1 == kInv);
-  if (d.has_chirp) {
-    apply_chirp<float, L, COL, E>(a, d, t, line0, d.fscale);
-    apply_chirp<float, L, COL, E>(b, d, t, line0 + 1, d.fscale);
-  } else if (d.scale_only) {
+  float2* out = reinterpret_cast<float2*>(d.out);
+  if (d.x2.ntr > 0) {
+    // the pass as a packed program (as in the line-pair kernel): both lines in
+    // FP32x2 lanes from load to store, inverses run in the J domain (parts
+    // swapped) on the forward codelets, each step between transforms switches
+    // domain, chirp products packed
+    using F = LineFftX2<L, PP, E, false>;
+    const X2Const K;
+    const bool finv = d.x2_first_inv != 0;
+    const bool linv = finv != (((d.x2.ntr - 1) & 1) != 0);
+    cx2 v[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-      a[s] = make_float2(a[s].x * d.fscale, a[s].y * d.fscale);
-      b[s] = make_float2(b[s].x * d.fscale, b[s].y * d.fscale);
+      const f32x2 re = x2_pack(a[s].x, b[s].x), im = x2_pack(a[s].y, b[s].y);
+      v[s] = finv ? cx2{im, re} : cx2{re, im};
     }
+    if (d.x2.pre.kind) x2_step_e<L, E, COL, false>(v, d.x2.pre, finv, d, t, line0);
+#pragma unroll 1
+    for (int k = 0; k < d.x2.ntr; ++k) {
+      if (k > 0) {
+        const X2Step st = k == 1 ? d.x2.gap[0] : d.x2.gap[1];
+        x2_step_e<L, E, COL, true>(v, st, finv != (((k - 1) & 1) != 0), d, t, line0);
+      }
+      if constexpr (F::S > 1) __syncthreads();  // the previous user of the exchange buffer is done
+      F::template stages<0>(v, xs2, t, q, tw, K);
+    }
+    if (d.x2.post[0].kind) x2_step_e<L, E, COL, false>(v, d.x2.post[0], linv, d, t, line0);
+    if (d.x2.post[1].kind) x2_step_e<L, E, COL, false>(v, d.x2.post[1], linv, d, t, line0);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const cx2 w = linv ? cx2{v[s].im, v[s].re} : v[s];
+      x2_unpack(w.re, a[s].x, b[s].x);
+      x2_unpack(w.im, a[s].y, b[s].y);
+    }
+  } else {
+    if (d.t1 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t1 == kInv);
+    if (d.has_chirp) {
+      apply_chirp<float, L, COL, E>(a, d, t, line0, d.fscale);
+      apply_chirp<float, L, COL, E>(b, d, t, line0 + 1, d.fscale);
+    } else if (d.scale_only) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        a[s] = make_float2(a[s].x * d.fscale, a[s].y * d.fscale);
+        b[s] = make_float2(b[s].x * d.fscale, b[s].y * d.fscale);
+      }
+    }
+    if (d.t2 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t2 == kInv);
   }
-  if (d.t2 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t2 == kInv);
-  float2* out = reinterpret_cast<float2*>(d.out);
+  if (COL && d.out_tiled && line0 + 1 < nlines) {
+    // the two lines of a column pair at one row are one 16-byte half of a tile sector
+    float4* o4 = reinterpret_cast<float4*>(out);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const int e = t + T_LINE * s;
+      o4[((size_t)(e >> 1) * (2 * d.Ny) + (line0 >> 1) * 4 + (e & 1) * 2) >> 1] = make_float4(a[s].x, a[s].y, b[s].x, b[s].y);
+    }
+    return;
+  }
+  if constexpr (!COL && PP < 32) {
+    // rows: the thread of the neighbouring position e^1 (same line pair) is
+    // lane ^ PP; the two swap halves so that each stores one 16-byte vector:
+    // tiled, float4 e of the row pair; row-major, (line0[e], line0[e+1]) from
+    // the even position and (line1[e-1], line1[e]) from the odd one
+    // (every lane shuffles: a warp can hold a valid and an invalid pair; line
+    // counts are even, so a pair is valid as a whole)
+    const bool valid = line0 < nlines;
+    const bool odd = (t & 1) != 0;
+    float4* o4 = reinterpret_cast<float4*>(d.out_tiled ? out + (size_t)(line0 >> 1) * (2 * d.Ny)
+                                                       : out + (size_t)line0 * d.Ny);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const int e = t + T_LINE * s;
+      const float2 give = odd ? a[s] : b[s];
+      const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, give.x, PP), __shfl_xor_sync(0xffffffffu, give.y, PP));
+      const float4 q = odd ? make_float4(got.x, got.y, b[s].x, b[s].y) : make_float4(a[s].x, a[s].y, got.x, got.y);
+      if (valid) o4[d.out_tiled ? e : (odd ? (d.Ny + e - 1) / 2 : e / 2)] = q;
+    }
+    return;
+  }
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int line = line0 + h;

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "batch_common.h"
+#include "fft_pass.cuh"
 
 using namespace nslct;
 
@@ -211,6 +212,10 @@ int nslct_batch_bind(nslct_batch_t b, const void* const* in, void* const* out) {
     // the batched kernels run elems_per_thread(L) per thread: their twiddle tables
     for (int k = 0; k < 5; ++k) {
       d[k].tw = chain_pass_is_column(k) ? b->plans[f]->tw16_x : b->plans[f]->tw16_y;
+      // the packed batched kernel runs the pass as a program (x2.ntr = 0: not one)
+      const int mode = x2_program(d[k], d[k].x2);
+      if (mode == 0) d[k].x2.ntr = 0;
+      d[k].x2_first_inv = (mode == 2 || mode == 3) ? 1 : 0;
       descs[(size_t)k * b->n + f] = d[k];
     }
   }

@@ -1398,9 +1398,8 @@ template <int L> struct X2Fft {
 // conj: the data is held in the J domain, so the chirp is conjugated. SWAP:
 // the results go to the other parts (the step also switches domain); a swap
 // with no step is a multiply by one.
-template <int L, bool COL, bool SWAP>
-__device__ __forceinline__ void x2_step(cx2* v, const X2Step& st, bool conj, const PassDesc& d, int t, int line0) {
-  constexpr int E = PairShape<L>::E;
+template <int L, int E, bool COL, bool SWAP>
+__device__ __forceinline__ void x2_step_e(cx2* v, const X2Step& st, bool conj, const PassDesc& d, int t, int line0) {
   constexpr int T = L / E;
   if (st.kind == 1) {
     const int nl = COL ? d.Ny : d.Nx;  // length of the other axis
@@ -1456,6 +1455,12 @@ __device__ __forceinline__ void x2_step(cx2* v, const X2Step& st, bool conj, con
       v[s] = SWAP ? cx2{im, re} : cx2{re, im};
     }
   }
+}
+
+// x2_step with the line-pair kernel's elements per thread
+template <int L, bool COL, bool SWAP>
+__device__ __forceinline__ void x2_step(cx2* v, const X2Step& st, bool conj, const PassDesc& d, int t, int line0) {
+  x2_step_e<L, PairShape<L>::E, COL, SWAP>(v, st, conj, d, t, line0);
 }
 
 // Thread 0: copies of one panel (G line pairs from line `first`) into the
