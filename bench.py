@@ -63,15 +63,16 @@ PASS_KERNELS = {
 # K = 384) times the 128-output real-block DFT_R matrix, 2 * 384 * 128 / 64
 # flops; a pass runs two stages per 1D transform
 TC_FLOPS_PER_SAMPLE_STAGE = 2 * 384 * 128 // 64
-# the same for the batched kernel (256 fields {128..2048}^2, all batched; row
-# kernel: mean of passes 1, 3, 5; the 128-thread variant not captured) and
-# the adjoint kernel (64 x 1024^2)
 # the split-precision tcgen05 kernel (one capture of passes 1-3 of a forward,
 # profiles/pass_kernel_tc_4096x4096_ncu.md; rows: mean of passes 1 and 3)
 NCU_TRAFFIC_MIXED = {"pass_kernel_tc<1>": 214.6e6, "pass_kernel_tc<0>": 212.8e6}
 # ncu sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed / 100, same capture
 TC_PIPE_ACTIVE = {"pass_kernel_tc<1>": 0.195, "pass_kernel_tc<0>": 0.238}
-NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 256>": 2.171e9, "batch_pass_kernel<1, 256>": 2.137e9}
+# the same for the batched kernel (256 fields {128..2048}^2, all batched; row
+# kernel: mean of passes 1, 3, 5; profiles/batch_and_adjoint_kernels_dram.md)
+# and the adjoint kernel (64 x 1024^2)
+NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 256>": 2.171e9, "batch_pass_kernel<1, 256>": 2.137e9,
+                     "batch_pass_kernel<0, 128>": 2.146e9, "batch_pass_kernel<1, 128>": 2.134e9}
 NCU_TRAFFIC_GRAD = {"dual_pass_kernel<float, 1024, 0>": 2.088e9, "dual_pass_kernel<float, 1024, 1>": 2.089e9}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
@@ -721,7 +722,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default 50; 10 for --impl reference, whose step takes ~14 s)")
+                    help="timed steps (default 150, about 0.8 s of FP32 and 1.8 s of split-precision transforms, "
+                         "so that the clock sampler sees the timed region; 10 for --impl reference, whose step "
+                         "takes ~14 s)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -743,7 +746,7 @@ def main():
                     help="ABCD matrices per step (16 is the benchmark workload; fewer only for profiling captures)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 10 if args.impl == "reference" else 50
+        args.steps = 10 if args.impl == "reference" else 150
     global N_ABCD
     N_ABCD = max(1, min(16, args.n_abcd))
     world, rank, local = _dist_init(args)
