@@ -1,12 +1,15 @@
 // Batched passes: one persistent launch per pass covers every field of a batch
 // of fields with uneven sizes (each with its own ABCD plan).
 //
-// Work items are (field, panel) pairs, ordered largest line first, and handed
-// out dynamically through an atomic counter, so a CTA that finishes a small
-// panel takes the next one. Each item's panel is copied global -> shared with
-// 16-byte cp.async while the CTA still computes the previous item, exactly as
-// in the single-field kernels; the line length (a template parameter there) is
-// dispatched per item here. Five such launches (plus one counter reset) make
+// Work items are (field, panel) pairs, ordered largest line first; CTA b takes
+// items b, b + grid, b + 2 grid, ... (items hold near-equal sample counts, so
+// the static order balances, and every future item of a CTA is known). Each
+// item's panel is copied global -> shared with 16-byte cp.async while the CTA
+// still computes the previous item; the item's descriptor is copied to one of
+// three shared slots the same way one item earlier, and the item records are
+// read into registers further ahead, so that starting an item waits on no
+// global load but its panel. The line length (a template parameter in the
+// single-field kernels) is dispatched per item here. Five such launches make
 // one batched transform; they can be captured into one CUDA graph.
 #pragma once
 
@@ -110,6 +113,39 @@ __device__ __forceinline__ void bstage_panel(float2* stg, const PassDesc& d, int
   }
 }
 
+// Copy a pass descriptor global -> shared with 8-byte cp.async (every thread
+// takes part; committed with the next cp_async_commit).
+template <int TH>
+__device__ __forceinline__ void bdesc_copy(PassDesc* dst, const PassDesc* src) {
+  static_assert(sizeof(PassDesc) % 8 == 0 && alignof(PassDesc) >= 8, "descriptor copy by 8-byte words");
+  constexpr int W = (int)(sizeof(PassDesc) / 8);
+  for (int w = threadIdx.x; w < W; w += TH)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(reinterpret_cast<uint64_t*>(dst) + w)),
+                 "l"(reinterpret_cast<const uint64_t*>(src) + w)
+                 : "memory");
+}
+
+// What an item does for the pipeline once its panel is in registers: stage the
+// next item's panel (its descriptor `nd` already in shared memory; null: no
+// next item) and copy the descriptor of the item after it (`cs`, null: none)
+// into the free slot `cd`.
+struct BNext {
+  const PassDesc* nd;
+  int npanel;
+  const PassDesc* cs;
+  PassDesc* cd;
+};
+
+template <bool COL, int TH>
+__device__ __forceinline__ void bstage_any(float2* stg, const PassDesc& d, int panel);
+
+template <bool COL, int TH>
+__device__ __forceinline__ void bprefetch(float2* stg, const BNext& nx) {
+  if (nx.cs) bdesc_copy<TH>(nx.cd, nx.cs);
+  if (nx.nd) bstage_any<COL, TH>(stg, *nx.nd, nx.npanel);
+  else cp_async_commit();
+}
+
 template <bool COL, int TH>
 __device__ __forceinline__ void bstage_any(float2* stg, const PassDesc& d, int panel) {
   const int L = COL ? d.Nx : d.Ny;
@@ -128,9 +164,7 @@ __device__ __forceinline__ void bstage_any(float2* stg, const PassDesc& d, int p
 // Compute one item whose panel sits in `stg`; prefetch `next` (if any) into
 // `stg` once the panel is in registers.
 template <int L, bool COL, int TH>
-__device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* stg, float2* xs,
-                                         const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items,
-                                         int next, int nitems) {
+__device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* stg, float2* xs, const BNext& nx) {
   using Sh = BShape<L, TH>;
   constexpr int E = Sh::E;
   constexpr int T_LINE = Sh::T_LINE;
@@ -145,10 +179,7 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
 #pragma unroll
   for (int s = 0; s < E; ++s) v[s] = stg[bstg_index<L, COL, TH>(p, t + T_LINE * s, d.in_tiled)];
   __syncthreads();  // staging consumed
-  if (next < nitems) {
-    const BatchItem it = items[next];
-    bstage_any<COL, TH>(stg, descs[it.field], it.panel);
-  }
+  bprefetch<COL, TH>(stg, nx);
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   if (d.t1 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t1 == kInv);
   if (d.has_chirp) {
@@ -174,9 +205,7 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
 // 2q and 2q + 1 at positions t + T_LINE s; both lines' FFTs run as one packed
 // FFT, the chirp per line.
 template <int L, bool COL, int TH>
-__device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2* stg, float2* xs,
-                                            const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items,
-                                            int next, int nitems) {
+__device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2* stg, float2* xs, const BNext& nx) {
   using Sh = BShape<L, TH>;
   constexpr int E = Sh::E;
   constexpr int T_LINE = Sh::T_LINE;
@@ -194,10 +223,7 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
     b[s] = stg[bstg_index<L, COL, TH>(2 * q + 1, t + T_LINE * s, d.in_tiled)];
   }
   __syncthreads();  // staging consumed
-  if (next < nitems) {
-    const BatchItem it = items[next];
-    bstage_any<COL, TH>(stg, descs[it.field], it.panel);
-  }
+  bprefetch<COL, TH>(stg, nx);
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   ulonglong2* xs2 = reinterpret_cast<ulonglong2*>(xs);
   float2* out = reinterpret_cast<float2*>(d.out);
@@ -295,56 +321,69 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
 }
 
 // One pass of the batch. descs[f] is field f's descriptor for this pass;
-// items[0..nitems) the work list; *counter must be 0 at launch.
+// items[0..nitems) the work list; *counter must be 0 at launch. Item indices
+// come from the counter three items ahead of use, item records two ahead and
+// descriptors one ahead, so that an item starts without a global load.
 template <bool COL, int TH>
 __global__ void __launch_bounds__(TH, TH == 128 ? 3 : (TH <= 256 ? 2 : 1))
 batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_item[2];
-  // the current item's descriptor, copied once per item: every thread reads
-  // many of its fields, which from global memory cost a load latency each
-  __shared__ __align__(16) PassDesc s_desc;
-  static_assert(sizeof(PassDesc) % 4 == 0, "descriptor copy by words");
+  // descriptors of the current item, the next one (its panel is staged from
+  // it) and the one after (being copied)
+  __shared__ __align__(16) PassDesc s_desc[3];
+  __shared__ int s_idx[4];
   float2* xs = reinterpret_cast<float2*>(smem_raw);
   // the exchange buffer (sized for the largest need) comes first, staging after it
   float2* stg = xs + batch_xsm<TH>();
-  if (threadIdx.x == 0) s_item[0] = atomicAdd(counter, 1);
-  __syncthreads();
-  int cur = s_item[0];
-  if (cur < nitems) {
-    const BatchItem it = items[cur];
-    bstage_any<COL, TH>(stg, descs[it.field], it.panel);
+  if (threadIdx.x == 0) {
+    const int base = atomicAdd(counter, 3);  // the first three items, consecutive
+    s_idx[0] = base;
+    s_idx[1] = base + 1;
+    s_idx[2] = base + 2;
+    s_idx[3] = atomicAdd(counter, 1);
   }
-  while (cur < nitems) {
-    if (threadIdx.x == 0) s_item[1] = atomicAdd(counter, 1);
+  __syncthreads();
+  auto item_at = [&](int k) { return k < nitems ? items[k] : BatchItem{-1, 0}; };
+  if (s_idx[0] >= nitems) return;
+  BatchItem it0 = items[s_idx[0]], it1 = item_at(s_idx[1]), it2 = item_at(s_idx[2]);
+  int idx3 = s_idx[3];
+  bdesc_copy<TH>(&s_desc[0], descs + it0.field);
+  if (it1.field >= 0) bdesc_copy<TH>(&s_desc[1], descs + it1.field);
+  bstage_any<COL, TH>(stg, descs[it0.field], it0.panel);
+  for (int i = 0; it0.field >= 0; ++i) {
+    // thread 0: the index of the item four on (stored once this item's
+    // barriers have passed); every thread: the record of the item three on
+    int idx4 = 0;
+    if (threadIdx.x == 0) idx4 = atomicAdd(counter, 1);
+    const BatchItem it3 = item_at(idx3);
     cp_async_wait_all();
     __syncthreads();
-    const int next = s_item[1];
-    const BatchItem it = items[cur];
-    {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(descs + it.field);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_desc);
-      for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += TH) dst[w] = src[w];
-    }
-    __syncthreads();
-    const PassDesc& d = s_desc;
+    const int slot = i % 3;
+    const PassDesc& d = s_desc[slot];
+    const BNext nx{it1.field >= 0 ? &s_desc[(slot + 1) % 3] : nullptr, it1.panel,
+                   it2.field >= 0 ? descs + it2.field : nullptr, &s_desc[(slot + 2) % 3]};
     const int L = COL ? d.Nx : d.Ny;
     switch (L) {
-#define NSLCT_BCASE(LL)                                                                   \
-  case LL:                                                                                \
-    if constexpr (BShape<LL, TH>::ok) {                                                   \
-      if constexpr (BShape<LL, TH>::PACKED)                                               \
-        bprocess_x2<LL, COL, TH>(d, it.panel, stg, xs, descs, items, next, nitems);       \
-      else                                                                                \
-        bprocess<LL, COL, TH>(d, it.panel, stg, xs, descs, items, next, nitems);          \
-    }                                                                                     \
+#define NSLCT_BCASE(LL)                                                   \
+  case LL:                                                                \
+    if constexpr (BShape<LL, TH>::ok) {                                   \
+      if constexpr (BShape<LL, TH>::PACKED)                               \
+        bprocess_x2<LL, COL, TH>(d, it0.panel, stg, xs, nx);              \
+      else                                                                \
+        bprocess<LL, COL, TH>(d, it0.panel, stg, xs, nx);                 \
+    }                                                                     \
     break;
       NSLCT_BATCH_LENGTHS(NSLCT_BCASE)
 #undef NSLCT_BCASE
       default: break;
     }
-    __syncthreads();  // everyone is done with s_item[1] and the exchange buffer
-    cur = next;
+    // every thread read s_idx[3] before this item's first barrier
+    if (threadIdx.x == 0) s_idx[3] = idx4;
+    __syncthreads();  // everyone is done with the exchange buffer, this item's descriptor slot and s_idx
+    idx3 = s_idx[3];
+    it0 = it1;
+    it1 = it2;
+    it2 = it3;
   }
   cp_async_wait_all();
 }
