@@ -60,10 +60,20 @@ __host__ __device__ constexpr int batch_stg() {
 #undef NSLCT_BSM
   return m;
 }
-template <int TH> constexpr size_t batch_smem() { return (size_t)(batch_xsm<TH>() + batch_stg<TH>()) * sizeof(float2); }
+// 128-thread CTAs stage each panel in the exchange buffer itself (four CTAs
+// per SM; the next panel is copied in once the item's last FFT has read the
+// buffer); the larger CTAs keep a separate staging buffer, filled while they
+// compute.
+template <int TH> __host__ __device__ constexpr bool batch_single_buffer() { return TH == 128; }
+template <int TH> __host__ __device__ constexpr int batch_ctas_per_sm() { return TH == 128 ? 4 : (TH == 256 ? 2 : 1); }
+template <int TH> constexpr size_t batch_smem() {
+  return (size_t)(batch_single_buffer<TH>() ? (batch_xsm<TH>() > batch_stg<TH>() ? batch_xsm<TH>() : batch_stg<TH>())
+                                            : batch_xsm<TH>() + batch_stg<TH>()) *
+         sizeof(float2);
+}
 static_assert(batch_smem<512>() <= 227 * 1024, "batched kernel shared memory");
 static_assert(batch_smem<256>() <= 113 * 1024, "two 256-thread batched CTAs per SM");
-static_assert(batch_smem<128>() <= 74 * 1024, "three 128-thread batched CTAs per SM");
+static_assert(batch_smem<128>() <= 52 * 1024, "four 128-thread batched CTAs per SM");
 
 // lines per panel for line length L with TH-thread CTAs (0: not handled)
 template <int TH>
@@ -179,7 +189,7 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
 #pragma unroll
   for (int s = 0; s < E; ++s) v[s] = stg[bstg_index<L, COL, TH>(p, t + T_LINE * s, d.in_tiled)];
   __syncthreads();  // staging consumed
-  bprefetch<COL, TH>(stg, nx);
+  if constexpr (!batch_single_buffer<TH>()) bprefetch<COL, TH>(stg, nx);
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   if (d.t1 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t1 == kInv);
   if (d.has_chirp) {
@@ -189,6 +199,10 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
     for (int s = 0; s < E; ++s) v[s] = make_float2(v[s].x * d.fscale, v[s].y * d.fscale);
   }
   if (d.t2 != kNone) LineFft<float, L, P, E>::run(v, xs, t, p, tw, d.t2 == kInv);
+  if constexpr (batch_single_buffer<TH>()) {
+    __syncthreads();  // the last FFT has read the buffer
+    bprefetch<COL, TH>(stg, nx);
+  }
   float2* out = reinterpret_cast<float2*>(d.out);
   if (valid) {
 #pragma unroll
@@ -202,8 +216,9 @@ __device__ __forceinline__ void bprocess(const PassDesc& d, int panel, float2* s
 }
 
 // bprocess for packed panels: thread (pair q, position group t) holds lines
-// 2q and 2q + 1 at positions t + T_LINE s; both lines' FFTs run as one packed
-// FFT, the chirp per line.
+// 2q and 2q + 1 at positions t + T_LINE s in the two FP32x2 lanes from load
+// to store. A pass program (d.x2.ntr > 0) runs as in the line-pair kernel;
+// any other pass unpacks into the generic packed FFT's operands.
 template <int L, bool COL, int TH>
 __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2* stg, float2* xs, const BNext& nx) {
   using Sh = BShape<L, TH>;
@@ -216,32 +231,28 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
   const int t = tid / PP;
   const int nlines = COL ? d.Ny : d.Nx;
   const int line0 = panel * P + 2 * q;
-  float2 a[E], b[E];
+  const bool prog = d.x2.ntr > 0;
+  // the pass program starts in the domain of its first transform (J for an
+  // inverse: parts swapped) and ends in that of its last
+  const bool finv = prog && d.x2_first_inv != 0;
+  const bool linv = prog && (finv != (((d.x2.ntr - 1) & 1) != 0));
+  cx2 v[E];
 #pragma unroll
   for (int s = 0; s < E; ++s) {
-    a[s] = stg[bstg_index<L, COL, TH>(2 * q, t + T_LINE * s, d.in_tiled)];
-    b[s] = stg[bstg_index<L, COL, TH>(2 * q + 1, t + T_LINE * s, d.in_tiled)];
+    const float2 a = stg[bstg_index<L, COL, TH>(2 * q, t + T_LINE * s, d.in_tiled)];
+    const float2 b = stg[bstg_index<L, COL, TH>(2 * q + 1, t + T_LINE * s, d.in_tiled)];
+    const f32x2 re = x2_pack(a.x, b.x), im = x2_pack(a.y, b.y);
+    v[s] = finv ? cx2{im, re} : cx2{re, im};
   }
   __syncthreads();  // staging consumed
-  bprefetch<COL, TH>(stg, nx);
+  if constexpr (!batch_single_buffer<TH>()) bprefetch<COL, TH>(stg, nx);
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(d.tw);
   ulonglong2* xs2 = reinterpret_cast<ulonglong2*>(xs);
-  float2* out = reinterpret_cast<float2*>(d.out);
-  if (d.x2.ntr > 0) {
-    // the pass as a packed program (as in the line-pair kernel): both lines in
-    // FP32x2 lanes from load to store, inverses run in the J domain (parts
-    // swapped) on the forward codelets, each step between transforms switches
-    // domain, chirp products packed
+  if (prog) {
+    // inverses run in the J domain on the forward codelets, each step between
+    // transforms switches domain, chirp products packed
     using F = LineFftX2<L, PP, E, false>;
     const X2Const K;
-    const bool finv = d.x2_first_inv != 0;
-    const bool linv = finv != (((d.x2.ntr - 1) & 1) != 0);
-    cx2 v[E];
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-      const f32x2 re = x2_pack(a[s].x, b[s].x), im = x2_pack(a[s].y, b[s].y);
-      v[s] = finv ? cx2{im, re} : cx2{re, im};
-    }
     if (d.x2.pre.kind) x2_step_e<L, E, COL, false>(v, d.x2.pre, finv, d, t, line0);
 #pragma unroll 1
     for (int k = 0; k < d.x2.ntr; ++k) {
@@ -254,13 +265,13 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
     }
     if (d.x2.post[0].kind) x2_step_e<L, E, COL, false>(v, d.x2.post[0], linv, d, t, line0);
     if (d.x2.post[1].kind) x2_step_e<L, E, COL, false>(v, d.x2.post[1], linv, d, t, line0);
+  } else {
+    float2 a[E], b[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-      const cx2 w = linv ? cx2{v[s].im, v[s].re} : v[s];
-      x2_unpack(w.re, a[s].x, b[s].x);
-      x2_unpack(w.im, a[s].y, b[s].y);
+      x2_unpack(v[s].re, a[s].x, b[s].x);
+      x2_unpack(v[s].im, a[s].y, b[s].y);
     }
-  } else {
     if (d.t1 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t1 == kInv);
     if (d.has_chirp) {
       apply_chirp<float, L, COL, E>(a, d, t, line0, d.fscale);
@@ -273,14 +284,25 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
       }
     }
     if (d.t2 != kNone) LineFftX2<L, PP, E, false>::run(a, b, xs2, t, q, tw, d.t2 == kInv);
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = cx2{x2_pack(a[s].x, b[s].x), x2_pack(a[s].y, b[s].y)};
   }
+  if constexpr (batch_single_buffer<TH>()) {
+    __syncthreads();  // the last FFT has read the buffer
+    bprefetch<COL, TH>(stg, nx);
+  }
+  float2* out = reinterpret_cast<float2*>(d.out);
   if (COL && d.out_tiled && line0 + 1 < nlines) {
     // the two lines of a column pair at one row are one 16-byte half of a tile sector
     float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll
     for (int s = 0; s < E; ++s) {
       const int e = t + T_LINE * s;
-      o4[((size_t)(e >> 1) * (2 * d.Ny) + (line0 >> 1) * 4 + (e & 1) * 2) >> 1] = make_float4(a[s].x, a[s].y, b[s].x, b[s].y);
+      const cx2 w = linv ? cx2{v[s].im, v[s].re} : v[s];
+      float a0, a1, b0, b1;
+      x2_unpack(w.re, a0, a1);
+      x2_unpack(w.im, b0, b1);
+      o4[((size_t)(e >> 1) * (2 * d.Ny) + (line0 >> 1) * 4 + (e & 1) * 2) >> 1] = make_float4(a0, b0, a1, b1);
     }
     return;
   }
@@ -298,23 +320,31 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
 #pragma unroll
     for (int s = 0; s < E; ++s) {
       const int e = t + T_LINE * s;
-      const float2 give = odd ? a[s] : b[s];
+      const cx2 w = linv ? cx2{v[s].im, v[s].re} : v[s];
+      float r0, r1, i0, i1;
+      x2_unpack(w.re, r0, r1);
+      x2_unpack(w.im, i0, i1);
+      const float2 give = odd ? make_float2(r0, i0) : make_float2(r1, i1);
       const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, give.x, PP), __shfl_xor_sync(0xffffffffu, give.y, PP));
-      const float4 q = odd ? make_float4(got.x, got.y, b[s].x, b[s].y) : make_float4(a[s].x, a[s].y, got.x, got.y);
-      if (valid) o4[d.out_tiled ? e : (odd ? (d.Ny + e - 1) / 2 : e / 2)] = q;
+      const float4 o = odd ? make_float4(got.x, got.y, r1, i1) : make_float4(r0, i0, got.x, got.y);
+      if (valid) o4[d.out_tiled ? e : (odd ? (d.Ny + e - 1) / 2 : e / 2)] = o;
     }
     return;
   }
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int line = line0 + h;
-    if (line < nlines) {
+  for (int s = 0; s < E; ++s) {
+    const int e = t + T_LINE * s;
+    const cx2 w = linv ? cx2{v[s].im, v[s].re} : v[s];
+    float r0, r1, i0, i1;
+    x2_unpack(w.re, r0, r1);
+    x2_unpack(w.im, i0, i1);
 #pragma unroll
-      for (int s = 0; s < E; ++s) {
-        const int e = t + T_LINE * s;
+    for (int h = 0; h < 2; ++h) {
+      const int line = line0 + h;
+      if (line < nlines) {
         const int i = COL ? e : line;
         const int j = COL ? line : e;
-        out[elem_index(i, j, d.Ny, d.out_tiled)] = h ? b[s] : a[s];
+        out[elem_index(i, j, d.Ny, d.out_tiled)] = h ? make_float2(r1, i1) : make_float2(r0, i0);
       }
     }
   }
@@ -325,7 +355,7 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
 // come from the counter three items ahead of use, item records two ahead and
 // descriptors one ahead, so that an item starts without a global load.
 template <bool COL, int TH>
-__global__ void __launch_bounds__(TH, TH == 128 ? 3 : (TH <= 256 ? 2 : 1))
+__global__ void __launch_bounds__(TH, batch_ctas_per_sm<TH>())
 batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // descriptors of the current item, the next one (its panel is staged from
@@ -333,8 +363,9 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
   __shared__ __align__(16) PassDesc s_desc[3];
   __shared__ int s_idx[4];
   float2* xs = reinterpret_cast<float2*>(smem_raw);
-  // the exchange buffer (sized for the largest need) comes first, staging after it
-  float2* stg = xs + batch_xsm<TH>();
+  // the exchange buffer (sized for the largest need) comes first, staging after
+  // it or (single buffer) in it
+  float2* stg = batch_single_buffer<TH>() ? xs : xs + batch_xsm<TH>();
   if (threadIdx.x == 0) {
     const int base = atomicAdd(counter, 3);  // the first three items, consecutive
     s_idx[0] = base;

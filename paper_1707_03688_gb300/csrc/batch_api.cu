@@ -98,7 +98,7 @@ void drop_graph(nslct_batch_s* b) {
 // (its counter must be zero).
 int launch_batched_pass(nslct_batch_s* b, int k, cudaStream_t s) {
   if (b->nitems[k] == 0) return NSLCT_OK;
-  const int grid = std::min(b->nitems[k], (b->threads == 128 ? 3 : b->threads == 256 ? 2 : 1) * b->num_sms);
+  const int grid = std::min(b->nitems[k], (b->threads == 128 ? 4 : b->threads == 256 ? 2 : 1) * b->num_sms);
   const PassDesc* descs = b->d_descs + (size_t)k * b->n;
   const BatchItem* items = b->d_items + b->item_off[k];
   return chain_pass_is_column(k)
