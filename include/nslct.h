@@ -429,10 +429,9 @@ int nslct_batch_capture(nslct_batch_t batch, nslct_stream_t stream);
  */
 int nslct_batch_set_split(nslct_batch_t batch, int split);
 int nslct_batch_get_split(nslct_batch_t batch);
-/* nslct_batch_threads -- the CTA size of the batched kernels: 256 (two CTAs per
- * SM; the default when every line is at most 2048 points), 512, or 128 (three
- * CTAs per SM, power-of-two lines as packed pairs; chosen only by
- * nslct_batch_tune). */
+/* nslct_batch_threads -- the CTA size of the batched kernels: 128 (four CTAs
+ * per SM, power-of-two lines as packed pairs; the default when every line is
+ * at most 2048 points), 256 (two CTAs per SM) or 512 (any length). */
 int nslct_batch_threads(nslct_batch_t batch);
 /* nslct_batch_set_threads -- pin the batched kernels' CTA size (128, 256 or
  * 512, else NSLCT_E_ARG). NSLCT_E_SIZE if some field has a line that size does

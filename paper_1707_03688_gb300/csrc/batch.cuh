@@ -24,7 +24,7 @@ namespace nslct {
 
 // Three CTA sizes: 512 threads (one CTA per SM, every length), 256 threads
 // (two CTAs per SM with independent barriers, lines up to 2048: a panel needs
-// at least two lines of L/E threads each) and 128 threads (three CTAs per SM).
+// at least two lines of L/E threads each) and 128 threads (four CTAs per SM).
 // With 128 threads, power-of-two lines up to 2048 run packed: each thread
 // holds the same positions of two lines as the two FP32x2 lanes
 // (pair_x2.cuh, LineFftX2), so a panel has twice the lines of its threads.

@@ -24,7 +24,7 @@ struct nslct_batch_s {
   // kernels (nslct_forward) instead of the batched launches; chosen by
   // nslct_batch_tune (default: every field batched)
   int split = 1 << 30;
-  int threads = 512;   // CTA size of the batched kernels: 256 when every line is <= 2048 (the tuner may pick 128)
+  int threads = 512;   // CTA size of the batched kernels: the smallest that handles every line (tuned)
   std::vector<int> Nx, Ny;
   // the fields that run alone are spread over these streams (forked from and
   // joined to the caller's stream by events), so their passes overlap
@@ -147,15 +147,14 @@ int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const 
   nslct_batch_s* b = new (std::nothrow) nslct_batch_s();
   if (!b) return NSLCT_E_NOMEM;
   b->n = nfields;
-#ifndef NSLCT_BATCH_THREADS
-#define NSLCT_BATCH_THREADS 256
-#endif
+  // the smallest CTA size that handles every line (the tuner may change it)
   b->threads = 512;
-  if (NSLCT_BATCH_THREADS == 256) {
-    bool all256 = true;
-    for (int f = 0; f < nfields && all256; ++f)
-      all256 = batch_panel_lines(Nx[f], 256) != 0 && batch_panel_lines(Ny[f], 256) != 0;
-    if (all256) b->threads = 256;
+  for (int th : {256, 128}) {
+    bool fits = true;
+    for (int f = 0; f < nfields && fits; ++f)
+      fits = batch_panel_lines(Nx[f], th) != 0 && batch_panel_lines(Ny[f], th) != 0;
+    if (!fits) break;
+    b->threads = th;
   }
   if (cudaGetDevice(&b->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
@@ -271,7 +270,7 @@ int nslct_batch_tune(nslct_batch_t b, nslct_stream_t stream, int iters, int* cho
     return NSLCT_E_CUDA;
   }
   // the batched kernels' CTA size is the other tuned choice: 128 threads
-  // (three CTAs per SM, packed line pairs), 256 (two CTAs per SM) or 512,
+  // (four CTAs per SM, packed line pairs), 256 (two CTAs per SM) or 512,
   // each where every field's lines fit it
   std::vector<int> tile = {512};
   for (int th : {256, 128}) {
