@@ -84,7 +84,7 @@ constexpr int BAR_TAB = 0, BAR_DONE = 1, BAR_DRAIN = 3, NBAR = 3 + NWARP;
 // then: TMEM base, abort flag, arrival counters [2]; then two buffers of the
 // scale exchange, each [4][128] quarter-row maxima and [NWARP] warp maxima
 constexpr uint32_t OFF_SCALE = OFF_X + NBAR * 8 + 16;
-constexpr uint32_t SCALE_FLOATS = 4 * 128 + NWARP;
+constexpr uint32_t SCALE_FLOATS = 4 * 128 + 2 * NWARP;
 constexpr uint32_t SMEM = OFF_SCALE + 2 * SCALE_FLOATS * 4;
 static_assert(SMEM <= 227 * 1024, "one CTA per SM");
 
@@ -375,19 +375,21 @@ __device__ __forceinline__ void operand_ready(Ctx& c, int slot, bool kmajor) {
 // before the factor `pre` that the caller still has to apply (a power of
 // two, folded into the row scale here).
 __device__ __forceinline__ void write_kmajor(Ctx& c, Slot& sl, int slot, const Vals& x, float mx) {
+  // the warp's maximum per line: its lanes with the same bit 3 hold one line
   float wm = mx;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+  for (int o = 16; o > 0; o >>= 1)
+    if (o != 8) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
   float* qmax = c.scale + (c.kjob & 1u) * SCALE_FLOATS;  // alternate buffers: the previous
   float* wmax = qmax + 4 * 128;                          // exchange may still be read
   c.kjob++;
   qmax[c.h * 128 + c.m] = mx;
-  if (c.lane == 0) wmax[c.w] = wm;
+  if ((c.lane & ~8) == 0) wmax[2 * c.w + c.line] = wm;
   cta_sync();
   const float rowmax = fmaxf(fmaxf(qmax[c.m], qmax[128 + c.m]), fmaxf(qmax[256 + c.m], qmax[384 + c.m]));
   float linemax = 0.f;
 #pragma unroll
-  for (int hh = 0; hh < 4; ++hh) linemax = fmaxf(linemax, fmaxf(wmax[4 * hh + 2 * c.line], wmax[4 * hh + 2 * c.line + 1]));
+  for (int w = 0; w < NWARP; ++w) linemax = fmaxf(linemax, wmax[2 * w + c.line]);
   sl.s_row = scale_exp(rowmax);
   sl.s_line = scale_exp(linemax);
   const f32x2 f = x2_bcast(pow2f(sl.s_row));
@@ -424,8 +426,9 @@ __device__ __forceinline__ void read_d(Ctx& c, int slot, Vals& x) {
 
 // After a transform's first stage: row n2's outputs Y[k1], k1 = 16 h + j, to
 // the line scale and times W_L^{n2 k1} = T[k1 / 8][n2] P[k1 % 8][n2] (the scale
-// folded into T), split, and written MN-major into column K(n2, re/im) of rows
-// line*64 + k1 of the slot's shared-memory A operand.
+// folded into T), split, and written MN-major into column K(n2, re/im) of the
+// slot's shared-memory A operand, at the row that holds (line, k1): 16 (k1 / 8)
+// + 8 line + k1 % 8 (the thread mapping of pass_kernel_tc).
 __device__ __forceinline__ void job_mid(Ctx& c, Slot& sl, int slot) {
   Vals x;
   read_d(c, slot, x);
@@ -448,8 +451,9 @@ __device__ __forceinline__ void job_mid(Ctx& c, Slot& sl, int slot) {
   unsigned char* alo = ahi + A_BYTES;
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
-    // rows line*64 + 16 h + 8 g + 0..7: core-matrix row group line*8 + 2 h + g
-    const uint32_t rowg = (uint32_t)(c.line * 8 + 2 * c.h + g) * A_CMN;
+    // k1 = 16 h + 8 g + 0..7: rows 16 (2 h + g) + 8 line + 0..7, core-matrix
+    // row group 4 h + 2 g + line
+    const uint32_t rowg = (uint32_t)(4 * c.h + 2 * g + c.line) * A_CMN;
 #pragma unroll
     for (int comp = 0; comp < 2; ++comp) {
       const int K = 4 * (c.r >> 1) + 2 * comp + (c.r & 1);
@@ -596,9 +600,14 @@ pass_kernel_tc(PassDesc d, const __grid_constant__ CUtensorMap map_in, int col_m
   c.q = warp & 3;
   c.h = warp >> 2;
   c.lane = lane;
+  // Tile row m (the thread's TMEM lane) holds index r of line `line`, m = 16 (r / 8)
+  // + 8 line + r % 8: a warp holds 16 consecutive indices of both lines of the
+  // tile, so that its global accesses cover whole 32-byte sectors of the 2x2-
+  // tiled layout (both lines of a pair at two consecutive indices) in row and
+  // column passes alike. Both stages use this order for their rows.
   c.m = 32 * c.q + lane;
-  c.line = c.m / R;
-  c.r = c.m % R;
+  c.line = (c.m >> 3) & 1;
+  c.r = 8 * (c.m >> 4) + (c.m & 7);
   c.tbase = *s_tbase;
   c.sbase = smem_u32(smem);
   c.smem = smem;
