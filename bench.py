@@ -65,9 +65,9 @@ PASS_KERNELS = {
 TC_FLOPS_PER_SAMPLE_STAGE = 2 * 384 * 128 // 64
 # the split-precision tcgen05 kernel (one capture of passes 1-3 of a forward,
 # profiles/pass_kernel_tc_4096x4096_ncu.md; rows: mean of passes 1 and 3)
-NCU_TRAFFIC_MIXED = {"pass_kernel_tc<1>": 214.6e6, "pass_kernel_tc<0>": 212.8e6}
+NCU_TRAFFIC_MIXED = {"pass_kernel_tc<1>": 215.0e6, "pass_kernel_tc<0>": 213.3e6}
 # ncu sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed / 100, same capture
-TC_PIPE_ACTIVE = {"pass_kernel_tc<1>": 0.195, "pass_kernel_tc<0>": 0.238}
+TC_PIPE_ACTIVE = {"pass_kernel_tc<1>": 0.226, "pass_kernel_tc<0>": 0.249}
 # the same for the batched kernel (256 fields {128..2048}^2, all batched; row
 # kernel: mean of passes 1, 3, 5; profiles/batch_and_adjoint_kernels_dram.md)
 # and the adjoint kernel (64 x 1024^2)
