@@ -561,6 +561,98 @@ def run_batch_workload(args, world, rank):
     b.close()
 
 
+def _fft_chain_tables(params, nx, ny, dx, dy, device, cdtype):
+    """Chirp tables of the chain for a library FFT (context only, not the
+    product): chi_H and chi_B' over FFT bins (centred frequency k(b) = b for
+    b < N/2, b - N above; spacing 2 pi / (N d); sign -), CM^{C2} and CM^{C1}
+    over centred samples (sign +). Phases in FP64, tables in `cdtype`."""
+    import torch
+
+    def quad(c, a, b, da, db, sign):
+        c = np.asarray(c, dtype=np.float64)
+        c12 = 0.5 * (c[0, 1] + c[1, 0])
+        ph = 0.5 * (c[0, 0] * (a * da) ** 2 + 2.0 * c12 * (a * da) * (b * db) + c[1, 1] * (b * db) ** 2)
+        return torch.polar(torch.ones_like(ph), sign * ph).to(cdtype)
+
+    f64 = dict(dtype=torch.float64, device=device)
+    bx, by = torch.arange(nx, **f64), torch.arange(ny, **f64)
+    kx = torch.where(bx < nx // 2, bx, bx - nx)[:, None]
+    ky = torch.where(by < ny // 2, by, by - ny)[None, :]
+    mx, my = (bx - nx // 2)[:, None], (by - ny // 2)[None, :]
+    dwx, dwy = 2 * math.pi / (nx * dx), 2 * math.pi / (ny * dy)
+    return (quad(params["H"], kx, ky, dwx, dwy, -1.0), quad(params["C2"], mx, my, dx, dy, 1.0),
+            quad(params["Bp"], kx, ky, dwx, dwy, -1.0), quad(params["C1"], mx, my, dx, dy, 1.0))
+
+
+def _fft_chain(x, tabs):
+    """CM^{C1} CC^{B'} CM^{C2} CC^{H} x with CC^B = -(1/(Nx Ny)) IFFT_u(chi_B FFT(.))
+    = -ifft2(chi_B fft2(.)); the two CCs' signs cancel."""
+    import torch
+    chi_h, cm2, chi_b, cm1 = tabs
+    y = torch.fft.fft2(x)
+    y.mul_(chi_h)
+    y = torch.fft.ifft2(y)
+    y.mul_(cm2)
+    y = torch.fft.fft2(y)
+    y.mul_(chi_b)
+    y = torch.fft.ifft2(y)
+    y.mul_(cm1)
+    return y
+
+
+def run_libfft_workload(args, world, rank):
+    """Context only, not the product: the same 16 transforms of the 4096^2
+    field as a library chain (torch.fft, i.e. cuFFT: two fft2, two ifft2 and
+    four table multiplies per transform, chirp tables precomputed from each
+    plan's own H, B', C1, C2), beside the library's fused passes on the same
+    GPU, and the two outputs' agreement."""
+    import torch
+    from paper_1707_03688_gb300 import nslct as N
+    N.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g, mats = _make_inputs()
+    plans = [N.Plan(m, NX, NY) for m in mats]
+    x = torch.from_numpy(g).to(torch.complex64).to(dev)
+    tabs = [_fft_chain_tables(p.params(), NX, NY, p.dx, p.dy, dev, torch.complex64) for p in plans]
+    outs = [torch.empty_like(x) for _ in plans]
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        ours = plans[0].forward(x)
+        lib = _fft_chain(x, tabs[0])
+        stream.synchronize()
+        agree = float((torch.linalg.vector_norm(lib - ours) / torch.linalg.vector_norm(ours)).item())
+
+        def lib_step():
+            for t in tabs:
+                _fft_chain(x, t)
+
+        def our_step():
+            for p, o in zip(plans, outs):
+                p.forward(x, out=o)
+
+        with ClockSampler(dev.index) as clk:
+            ms_lib = _timed(lib_step, args.steps, args.warmup, stream)
+            ms_ours = _timed(our_step, args.steps, args.warmup, stream)
+    samples = N_ABCD * NX * NY
+    line = {
+        "metric": "context: library-FFT chain vs the fused passes, forward NsDLCT Msamples/s",
+        "value": samples / (ms_lib * 1e-3) / 1e6, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_lib, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; torch.fft (cuFFT) chain with precomputed chirp tables, one stream",
+                   "nx": NX, "ny": NY, "n_abcd": N_ABCD},
+        "fused_same_run": {"value": samples / (ms_ours * 1e-3) / 1e6, "ms_per_step": ms_ours,
+                           "note": "nslct_forward per transform on one stream"},
+        "ratio_fused_over_library": ms_lib / ms_ours,
+        "rel_l2_library_vs_fused": agree,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
 def run_filter_workload(args, world, rank):
     """Filtering in two NsLCT domains (Sec. 5.B) on the 4096^2 field: Eq. Add04
     (two masked forwards, two inverses) and Eq. Add08 (two masked forwards,
@@ -729,9 +821,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="leave out the split-precision form that the default line reports beside FP32")
-    ap.add_argument("--workload", default="fp32", choices=["fp32", "batch", "grad", "filter"],
+    ap.add_argument("--workload", default="fp32", choices=["fp32", "batch", "grad", "filter", "libfft"],
                     help="fp32: 4096^2 x 16 ABCD (the benchmark line); batch: 256 uneven fields; "
-                         "grad: 64 x 1024^2 forward + backward; filter: two-domain filtering, Eqs. Add04/Add08")
+                         "grad: 64 x 1024^2 forward + backward; filter: two-domain filtering, Eqs. Add04/Add08; "
+                         "libfft: context only, the same transforms as a torch.fft (cuFFT) chain")
     ap.add_argument("--method", default="ha", choices=["ha", "lc_y"],
                     help="H of Eq. HA24 (five passes) or of Eq. LC10 (three passes)")
     ap.add_argument("--decomposition", default="type1", choices=["type1", "type2", "trace"],
@@ -757,6 +850,8 @@ def main():
         run_grad_workload(args, world, rank)
     elif args.workload == "filter":
         run_filter_workload(args, world, rank)
+    elif args.workload == "libfft":
+        run_libfft_workload(args, world, rank)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:
