@@ -22,20 +22,40 @@ namespace nslct {
 #define NSLCT_BATCH_LENGTHS(X) \
   X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(96) X(192) X(384) X(768) X(1536)
 
-// Three CTA sizes: 512 threads (one CTA per SM, every length), 256 threads
-// (two CTAs per SM with independent barriers, lines up to 2048: a panel needs
-// at least two lines of L/E threads each) and 128 threads (four CTAs per SM).
-// With 128 threads, power-of-two lines up to 2048 run packed: each thread
-// holds the same positions of two lines as the two FP32x2 lanes
-// (pair_x2.cuh, LineFftX2), so a panel has twice the lines of its threads.
-template <int L, int TH> constexpr bool batch_packed() { return TH == 128 && dual_x2_length<L>() && L <= 2048; }
+// CTA configurations (the template parameter TH below): 512 threads (one CTA
+// per SM, every length), 256 threads (two CTAs per SM with independent
+// barriers, lines up to 2048: a panel needs at least two lines of L/E threads
+// each), 128 threads (four CTAs per SM) and kB3K (batch_common.h), 128 threads for 3*2^a lines
+// alone (three CTAs per SM). Packed configurations hold the same positions of
+// two lines in each thread as the two FP32x2 lanes (pair_x2.cuh, LineFftX2),
+// so a panel has twice the lines of its threads: 128 threads pack power-of-two
+// lines up to 2048 (16 positions per line, 3*2^a lines run one per thread),
+// kB3K packs 3*2^a lines up to 1536 (24 positions per line: the registers of
+// three CTAs per SM, not four).
+__host__ __device__ constexpr int bthreads(int TH) { return TH % 1000; }
+template <int L> __host__ __device__ constexpr bool x2_3k_length() {
+  if constexpr (is_pow2(L) || L % 24 != 0 || L > 2048) return false;
+  else {
+    constexpr int E = elems_per_thread(L);
+    bool ok = E == 24 && stage_radix(L, E, 0) == 24;
+    for (int st = 1; st < num_stages(L, E); ++st) {
+      const int r = stage_radix(L, E, st);
+      ok = ok && (r == 2 || r == 4 || r == 8);
+    }
+    return ok;
+  }
+}
+template <int L, int TH> __host__ __device__ constexpr bool batch_packed() {
+  return TH == kB3K ? x2_3k_length<L>() : (TH == 128 && dual_x2_length<L>() && L <= 2048);
+}
 template <int L, int TH> struct BShape {
   static constexpr int E = elems_per_thread(L);  // the plans' tw16 tables
   static constexpr int T_LINE = L / E;
-  static constexpr int THREADS = TH;
+  static constexpr int THREADS = bthreads(TH);
   static constexpr bool PACKED = batch_packed<L, TH>();
-  static constexpr int P = (PACKED ? 2 : 1) * TH / T_LINE;  // lines per panel
-  static constexpr bool ok = P >= 2 && P % 2 == 0 && (PACKED ? P / 2 : P) * T_LINE == TH;
+  static constexpr int P = (PACKED ? 2 : 1) * THREADS / T_LINE;  // lines per panel
+  static constexpr bool ok = (TH != kB3K || PACKED) && P >= 2 && P % 2 == 0 &&
+                             (PACKED ? P / 2 : P) * T_LINE == THREADS;
   static constexpr int XSM = P * (L + L / 16);
   static constexpr int STG_ROW = P * (L + 8);  // row-major rows are padded in staging
   static constexpr int STG_TILED = P * L;
@@ -64,8 +84,10 @@ __host__ __device__ constexpr int batch_stg() {
 // per SM; the next panel is copied in once the item's last FFT has read the
 // buffer); the larger CTAs keep a separate staging buffer, filled while they
 // compute.
-template <int TH> __host__ __device__ constexpr bool batch_single_buffer() { return TH == 128; }
-template <int TH> __host__ __device__ constexpr int batch_ctas_per_sm() { return TH == 128 ? 4 : (TH == 256 ? 2 : 1); }
+template <int TH> __host__ __device__ constexpr bool batch_single_buffer() { return bthreads(TH) == 128; }
+template <int TH> __host__ __device__ constexpr int batch_ctas_per_sm() {
+  return TH == kB3K ? 3 : (TH == 128 ? 4 : (TH == 256 ? 2 : 1));
+}
 template <int TH> constexpr size_t batch_smem() {
   return (size_t)(batch_single_buffer<TH>() ? (batch_xsm<TH>() > batch_stg<TH>() ? batch_xsm<TH>() : batch_stg<TH>())
                                             : batch_xsm<TH>() + batch_stg<TH>()) *
@@ -74,6 +96,7 @@ template <int TH> constexpr size_t batch_smem() {
 static_assert(batch_smem<512>() <= 227 * 1024, "batched kernel shared memory");
 static_assert(batch_smem<256>() <= 113 * 1024, "two 256-thread batched CTAs per SM");
 static_assert(batch_smem<128>() <= 52 * 1024, "four 128-thread batched CTAs per SM");
+static_assert(batch_smem<kB3K>() <= 70 * 1024, "three packed 3*2^a CTAs per SM");
 
 // lines per panel for line length L with TH-thread CTAs (0: not handled)
 template <int TH>
@@ -102,21 +125,21 @@ __device__ __forceinline__ void bstage_panel(float2* stg, const PassDesc& d, int
   const int first = panel * P;
   if (COL) {
     const int tiles_valid = min(P, d.Ny - first) / 2;
-    for (int c = threadIdx.x; c < CHUNKS; c += TH) {
+    for (int c = threadIdx.x; c < CHUNKS; c += bthreads(TH)) {
       const int a = c / P, k = c % P;
       if ((k >> 1) < tiles_valid)
         cp_async16(stg + a * (2 * P) + k * 2, in + (size_t)a * (2 * d.Ny) + (first >> 1) * 4 + k * 2);
     }
   } else if (d.in_tiled) {
     const int rows_valid = min(P, d.Nx - first);
-    for (int c = threadIdx.x; c < CHUNKS; c += TH) {
+    for (int c = threadIdx.x; c < CHUNKS; c += bthreads(TH)) {
       const int q = c / L, k = c % L;
       if (2 * q < rows_valid) cp_async16(stg + q * (2 * L) + k * 2, in + (size_t)((first >> 1) + q) * (2 * L) + k * 2);
     }
   } else {
     constexpr int CPR = L / 2;
     const int rows_valid = min(P, d.Nx - first);
-    for (int c = threadIdx.x; c < CHUNKS; c += TH) {
+    for (int c = threadIdx.x; c < CHUNKS; c += bthreads(TH)) {
       const int q = c / CPR, k = c % CPR;
       if (q < rows_valid) cp_async16(stg + q * (L + 8) + k * 2, in + (size_t)(first + q) * L + k * 2);
     }
@@ -129,7 +152,7 @@ template <int TH>
 __device__ __forceinline__ void bdesc_copy(PassDesc* dst, const PassDesc* src) {
   static_assert(sizeof(PassDesc) % 8 == 0 && alignof(PassDesc) >= 8, "descriptor copy by 8-byte words");
   constexpr int W = (int)(sizeof(PassDesc) / 8);
-  for (int w = threadIdx.x; w < W; w += TH)
+  for (int w = threadIdx.x; w < W; w += bthreads(TH))
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(reinterpret_cast<uint64_t*>(dst) + w)),
                  "l"(reinterpret_cast<const uint64_t*>(src) + w)
                  : "memory");
@@ -355,7 +378,7 @@ __device__ __forceinline__ void bprocess_x2(const PassDesc& d, int panel, float2
 // come from the counter three items ahead of use, item records two ahead and
 // descriptors one ahead, so that an item starts without a global load.
 template <bool COL, int TH>
-__global__ void __launch_bounds__(TH, batch_ctas_per_sm<TH>())
+__global__ void __launch_bounds__(bthreads(TH), batch_ctas_per_sm<TH>())
 batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // descriptors of the current item, the next one (its panel is staged from
@@ -422,7 +445,9 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
 template <bool COL>
 inline int launch_batch(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems,
                         int* counter, cudaStream_t s) {
-  if (threads == 128)
+  if (threads == kB3K)
+    batch_pass_kernel<COL, kB3K><<<grid, 128, batch_smem<kB3K>(), s>>>(descs, items, nitems, counter);
+  else if (threads == 128)
     batch_pass_kernel<COL, 128><<<grid, 128, batch_smem<128>(), s>>>(descs, items, nitems, counter);
   else if (threads == 256)
     batch_pass_kernel<COL, 256><<<grid, 256, batch_smem<256>(), s>>>(descs, items, nitems, counter);
@@ -433,7 +458,9 @@ inline int launch_batch(int grid, int threads, const PassDesc* descs, const Batc
 
 template <bool COL>
 inline int prepare_batch() {
-  const bool ok = cudaFuncSetAttribute(batch_pass_kernel<COL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const bool ok = cudaFuncSetAttribute(batch_pass_kernel<COL, kB3K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_smem<kB3K>()) == cudaSuccess &&
+                  cudaFuncSetAttribute(batch_pass_kernel<COL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)batch_smem<128>()) == cudaSuccess &&
                   cudaFuncSetAttribute(batch_pass_kernel<COL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)batch_smem<256>()) == cudaSuccess &&

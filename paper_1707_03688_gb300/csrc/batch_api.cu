@@ -17,9 +17,12 @@ struct nslct_batch_s {
   std::vector<nslct_plan_t> plans;
   PassDesc* d_descs = nullptr;      // [5][n]
   BatchItem* d_items = nullptr;     // all passes' work lists back to back
-  int item_off[5] = {0};
-  int nitems[5] = {0};
-  int* d_counters = nullptr;        // one per pass
+  // per pass, up to two work lists: [0] the lines of the configuration
+  // `threads`; [1] (128-thread CTAs) the 3*2^a lines, which run packed in the
+  // kB3K configuration on a second stream, beside list [0]
+  int item_off[5][2] = {};
+  int nitems[5][2] = {};
+  int* d_counters = nullptr;        // one per pass and list
   // fields whose shorter side is >= split run through their own plan's fused
   // kernels (nslct_forward) instead of the batched launches; chosen by
   // nslct_batch_tune (default: every field batched)
@@ -31,6 +34,8 @@ struct nslct_batch_s {
   static constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, join[kSide] = {};
+  cudaStream_t xs = nullptr;        // the second list's stream
+  cudaEvent_t xfork = nullptr, xjoin = nullptr;
   bool bound = false;
   std::vector<const void*> in;
   std::vector<void*> out;
@@ -48,6 +53,9 @@ void free_batch(nslct_batch_s* b) {
     if (b->join[k]) cudaEventDestroy(b->join[k]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->xs) cudaStreamDestroy(b->xs);
+  if (b->xfork) cudaEventDestroy(b->xfork);
+  if (b->xjoin) cudaEventDestroy(b->xjoin);
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->d_descs) cudaFree(b->d_descs);
@@ -59,8 +67,23 @@ void free_batch(nslct_batch_s* b) {
 
 bool runs_alone(const nslct_batch_s* b, int f) { return std::min(b->Nx[f], b->Ny[f]) >= b->split; }
 
+#ifndef NSLCT_BATCH_B3K
+#define NSLCT_BATCH_B3K 1
+#endif
+// The configuration that runs lines of length L in a pass when the batch's CTA
+// size is `threads`: with 128 threads, the 3*2^a lines of column passes go to
+// the packed kB3K kernel (measured on the 256-field workload: column passes
+// 20 % faster for those fields; their one-FFT row passes 10-15 % slower at
+// three CTAs per SM, so rows stay in the four-CTA kernel).
+int line_config(int threads, int L, bool col) {
+  return (NSLCT_BATCH_B3K && threads == 128 && col && (L & (L - 1)) != 0 && batch_panel_lines(L, kB3K) > 0)
+             ? kB3K
+             : threads;
+}
+
 // (Re)build the per-pass work lists of the batched fields: every field's
-// panels, longest lines first.
+// panels, longest lines first, in the list of the configuration that runs
+// their lines.
 int build_items(nslct_batch_s* b) {
   std::vector<BatchItem> all;
   for (int k = 0; k < 5; ++k) {
@@ -72,14 +95,18 @@ int build_items(nslct_batch_s* b) {
       const int la = col ? b->Nx[a] : b->Ny[a], lc = col ? b->Nx[c] : b->Ny[c];
       return la > lc;
     });
-    b->item_off[k] = (int)all.size();
-    for (int f : order) {
-      const int L = col ? b->Nx[f] : b->Ny[f];
-      const int lines = col ? b->Ny[f] : b->Nx[f];
-      const int P = batch_panel_lines(L, b->threads);
-      for (int panel = 0; panel * P < lines; ++panel) all.push_back(BatchItem{f, panel});
+    for (int li = 0; li < 2; ++li) {
+      b->item_off[k][li] = (int)all.size();
+      for (int f : order) {
+        const int L = col ? b->Nx[f] : b->Ny[f];
+        const int cfg = line_config(b->threads, L, col);
+        if ((cfg == kB3K) != (li == 1)) continue;
+        const int lines = col ? b->Ny[f] : b->Nx[f];
+        const int P = batch_panel_lines(L, cfg);
+        for (int panel = 0; panel * P < lines; ++panel) all.push_back(BatchItem{f, panel});
+      }
+      b->nitems[k][li] = (int)all.size() - b->item_off[k][li];
     }
-    b->nitems[k] = (int)all.size() - b->item_off[k];
   }
   if (b->d_items) { cudaFree(b->d_items); b->d_items = nullptr; }
   if (all.empty()) return NSLCT_OK;
@@ -94,16 +121,31 @@ void drop_graph(nslct_batch_s* b) {
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
 }
 
-// Pass k of the batched fields: one persistent launch over its work items
-// (its counter must be zero).
-int launch_batched_pass(nslct_batch_s* b, int k, cudaStream_t s) {
-  if (b->nitems[k] == 0) return NSLCT_OK;
-  const int grid = std::min(b->nitems[k], (b->threads == 128 ? 4 : b->threads == 256 ? 2 : 1) * b->num_sms);
+// Pass k of the batched fields: one persistent launch over each non-empty work
+// list (their counters must be zero); the second list runs on its own stream,
+// forked from and joined back to `s`.
+int launch_list(nslct_batch_s* b, int k, int li, cudaStream_t s) {
+  const int n = b->nitems[k][li];
+  if (n == 0) return NSLCT_OK;
+  const int cfg = li == 1 ? kB3K : b->threads;
+  const int per_sm = cfg == kB3K ? 3 : cfg == 128 ? 4 : cfg == 256 ? 2 : 1;
+  const int grid = std::min(n, per_sm * b->num_sms);
   const PassDesc* descs = b->d_descs + (size_t)k * b->n;
-  const BatchItem* items = b->d_items + b->item_off[k];
-  return chain_pass_is_column(k)
-             ? launch_batch_col(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s)
-             : launch_batch_row(grid, b->threads, descs, items, b->nitems[k], b->d_counters + k, s);
+  const BatchItem* items = b->d_items + b->item_off[k][li];
+  int* counter = b->d_counters + 2 * k + li;
+  return chain_pass_is_column(k) ? launch_batch_col(grid, cfg, descs, items, n, counter, s)
+                                 : launch_batch_row(grid, cfg, descs, items, n, counter, s);
+}
+
+int launch_batched_pass(nslct_batch_s* b, int k, cudaStream_t s) {
+  if (b->nitems[k][1] == 0) return launch_list(b, k, 0, s);
+  if (cudaEventRecord(b->xfork, s) != cudaSuccess || cudaStreamWaitEvent(b->xs, b->xfork, 0) != cudaSuccess)
+    return NSLCT_E_CUDA;
+  int rc = launch_list(b, k, 1, b->xs);
+  if (rc == NSLCT_OK) rc = launch_list(b, k, 0, s);
+  if (cudaEventRecord(b->xjoin, b->xs) != cudaSuccess || cudaStreamWaitEvent(s, b->xjoin, 0) != cudaSuccess)
+    return NSLCT_E_CUDA;
+  return rc;
 }
 
 int enqueue(nslct_batch_s* b, cudaStream_t s) {
@@ -120,7 +162,7 @@ int enqueue(nslct_batch_s* b, cudaStream_t s) {
     const int rc = nslct_forward(b->plans[f], b->in[f], b->out[f], b->side[i++ % nside]);
     if (rc != NSLCT_OK) return rc;
   }
-  if (cudaMemsetAsync(b->d_counters, 0, 5 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
+  if (cudaMemsetAsync(b->d_counters, 0, 10 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
   for (int k = 0; k < 5; ++k) {
     const int rc = launch_batched_pass(b, k, s);
     if (rc != NSLCT_OK) return rc;
@@ -173,12 +215,15 @@ int nslct_plan_batch(nslct_batch_t* out, int nfields, const double* abcd, const 
   for (int k = 0; k < nslct_batch_s::kSide && ev_ok; ++k)
     ev_ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  ev_ok = ev_ok && cudaStreamCreateWithFlags(&b->xs, cudaStreamNonBlocking) == cudaSuccess &&
+          cudaEventCreateWithFlags(&b->xfork, cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventCreateWithFlags(&b->xjoin, cudaEventDisableTiming) == cudaSuccess;
   if (!ev_ok) {
     free_batch(b);
     return NSLCT_E_CUDA;
   }
   if (cudaMalloc(&b->d_descs, 5 * (size_t)nfields * sizeof(PassDesc)) != cudaSuccess ||
-      cudaMalloc(&b->d_counters, 5 * sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&b->d_counters, 10 * sizeof(int)) != cudaSuccess) {
     free_batch(b);
     return NSLCT_E_NOMEM;
   }
@@ -347,7 +392,7 @@ int nslct_batch_forward_pass(nslct_batch_t b, int pass, nslct_stream_t stream) {
     const int rc = nslct_forward_pass(b->plans[f], pass, b->in[f], b->out[f], stream);
     if (rc != NSLCT_OK) return rc;
   }
-  if (cudaMemsetAsync(b->d_counters + pass, 0, sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
+  if (cudaMemsetAsync(b->d_counters + 2 * pass, 0, 2 * sizeof(int), s) != cudaSuccess) return NSLCT_E_CUDA;
   return launch_batched_pass(b, pass, s);
 }
 

@@ -3,7 +3,8 @@
 
 namespace nslct {
 int batch_panel_lines(int L, int threads) {
-  return threads == 128   ? batch_lines_of<128>(L)
+  return threads == kB3K  ? batch_lines_of<kB3K>(L)
+         : threads == 128 ? batch_lines_of<128>(L)
          : threads == 256 ? batch_lines_of<256>(L)
          : threads == 512 ? batch_lines_of<512>(L)
                           : 0;

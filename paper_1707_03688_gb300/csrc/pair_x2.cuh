@@ -187,6 +187,41 @@ template <> struct X2Dft<16> {
   }
 };
 
+// Radix-3 DFT in place, W3 = e^{-2 pi i / 3} = -1/2 - i sqrt(3)/2:
+// X0 = a + (b + c), X1,2 = a - (b + c)/2 -/+ i sqrt(3)/2 (b - c).
+__device__ __forceinline__ void x2_dft3(cx2& a, cx2& b, cx2& c) {
+  const f32x2 mh = x2_bcast(-0.5f);
+  const f32x2 r3 = x2_bcast(0.86602540378443864676f), nr3 = x2_bcast(-0.86602540378443864676f);
+  const cx2 t = c2_add(b, c), d = c2_sub(b, c);
+  const cx2 m = {x2_fma(t.re, mh, a.re), x2_fma(t.im, mh, a.im)};
+  a = c2_add(a, t);
+  b = {x2_fma(d.im, r3, m.re), x2_fma(d.re, nr3, m.im)};
+  c = {x2_fma(d.im, nr3, m.re), x2_fma(d.re, r3, m.im)};
+}
+// 24 = 3 x 8 by the prime-factor (Good-Thomas) mapping, which needs no
+// twiddles between the two layers: n = (8 n1 + 3 n2) mod 24 and
+// k = (16 k1 + 9 k2) mod 24, so that W24^{nk} = W3^{n1 k1} W8^{n2 k2}.
+template <> struct X2Dft<24> {
+  static __device__ __forceinline__ void run(cx2* x, const X2Const& K) {
+    // radix 3 over n1 for each n2: slots (3 n2, 3 n2 + 8, 3 n2 + 16) mod 24
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) x2_dft3(x[(3 * n2) % 24], x[(3 * n2 + 8) % 24], x[(3 * n2 + 16) % 24]);
+    // radix 8 over n2 for each k1 (the slots (8 k1 + 3 n2) mod 24 of n1 = k1);
+    // X[(16 k1 + 9 k2) mod 24] is output k2 of group k1
+    cx2 t[3][8];
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+      for (int n2 = 0; n2 < 8; ++n2) t[k1][n2] = x[(8 * k1 + 3 * n2) % 24];
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) X2Dft<8>::run(t[k1], K);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) x[(16 * k1 + 9 * k2) % 24] = t[k1][k2];
+  }
+};
+
 // A twiddle factor in both lanes, with its negated sine.
 struct tw2 {
   f32x2 c, s, ns;
