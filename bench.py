@@ -549,7 +549,12 @@ def run_batch_workload(args, world, rank):
         "per_field_launches": {"ms_per_step": ms_each, "value": samples / (ms_each * 1e-3) / 1e6},
         "all_batched_no_graph": {"ms_per_step": ms_all_batched, "value": samples / (ms_all_batched * 1e-3) / 1e6},
         "tuned_no_graph": {"ms_per_step": ms_launch, "value": samples / (ms_launch * 1e-3) / 1e6},
-        "gpu_launches": 5 + 5 * sum(1 for nx, ny in shapes if min(nx, ny) >= split), "clocks": clk.summary(),
+        # five batched launches, plus one per column pass for the packed 3*2^a
+        # lines at 128-thread CTAs, plus five per field run alone
+        "gpu_launches": 5 + (2 if b.threads == 128 and any(
+            nx & (nx - 1) and min(nx, ny) < split for nx, ny in shapes) else 0)
+        + 5 * sum(1 for nx, ny in shapes if min(nx, ny) >= split),
+        "clocks": clk.summary(),
         # the batched kernel with every field batched, passes timed one by one
         "roofline": _dominant_roofline(pass_ms, [f"batch_pass_kernel<{int(chain_col)}, {th_all}>"
                                                  for chain_col in (0, 1, 0, 1, 0)],

@@ -445,9 +445,12 @@ batch_pass_kernel(const PassDesc* __restrict__ descs, const BatchItem* __restric
 template <bool COL>
 inline int launch_batch(int grid, int threads, const PassDesc* descs, const BatchItem* items, int nitems,
                         int* counter, cudaStream_t s) {
-  if (threads == kB3K)
-    batch_pass_kernel<COL, kB3K><<<grid, 128, batch_smem<kB3K>(), s>>>(descs, items, nitems, counter);
-  else if (threads == 128)
+  if (threads == kB3K) {
+    // column passes only (the batch's scheduler sends row passes' 3*2^a lines
+    // to the four-CTA kernel)
+    if constexpr (COL) batch_pass_kernel<COL, kB3K><<<grid, 128, batch_smem<kB3K>(), s>>>(descs, items, nitems, counter);
+    else return NSLCT_E_UNSUPPORTED;
+  } else if (threads == 128)
     batch_pass_kernel<COL, 128><<<grid, 128, batch_smem<128>(), s>>>(descs, items, nitems, counter);
   else if (threads == 256)
     batch_pass_kernel<COL, 256><<<grid, 256, batch_smem<256>(), s>>>(descs, items, nitems, counter);
@@ -458,9 +461,11 @@ inline int launch_batch(int grid, int threads, const PassDesc* descs, const Batc
 
 template <bool COL>
 inline int prepare_batch() {
-  const bool ok = cudaFuncSetAttribute(batch_pass_kernel<COL, kB3K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)batch_smem<kB3K>()) == cudaSuccess &&
-                  cudaFuncSetAttribute(batch_pass_kernel<COL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if constexpr (COL)
+    if (cudaFuncSetAttribute(batch_pass_kernel<COL, kB3K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem<kB3K>()) != cudaSuccess)
+      return NSLCT_E_CUDA;
+  const bool ok = cudaFuncSetAttribute(batch_pass_kernel<COL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)batch_smem<128>()) == cudaSuccess &&
                   cudaFuncSetAttribute(batch_pass_kernel<COL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)batch_smem<256>()) == cudaSuccess &&
