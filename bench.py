@@ -71,7 +71,7 @@ TC_PIPE_ACTIVE = {"pass_kernel_tc<1>": 0.226, "pass_kernel_tc<0>": 0.249}
 # the same for the batched kernel (256 fields {128..2048}^2, all batched; row
 # kernel: mean of passes 1, 3, 5; profiles/batch_and_adjoint_kernels_dram.md)
 # and the adjoint kernel (64 x 1024^2)
-NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 128>": 2.149e9, "batch_pass_kernel<1, 128>": 2.167e9}
+NCU_TRAFFIC_BATCH = {"batch_pass_kernel<0, 128>": 2.149e9}
 NCU_TRAFFIC_GRAD = {"dual_pass_kernel<float, 1024, 0>": 2.088e9, "dual_pass_kernel<float, 1024, 1>": 2.089e9}
 H_CHOICE = {"ha": "HA (Eq. HA24), five passes", "lc_y": "LC (Eq. LC10, H = (0,0;0,h)), three passes"}
 METRIC = "2D NsLCT Msamples/s and % HBM roofline, mixed vs FP32 at stated rel-L2 error"
