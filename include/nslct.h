@@ -431,7 +431,9 @@ int nslct_batch_set_split(nslct_batch_t batch, int split);
 int nslct_batch_get_split(nslct_batch_t batch);
 /* nslct_batch_threads -- the CTA size of the batched kernels: 128 (four CTAs
  * per SM, power-of-two lines as packed pairs; the default when every line is
- * at most 2048 points), 256 (two CTAs per SM) or 512 (any length). */
+ * at most 2048 points; in column passes, 3*2^a lines run packed in a second
+ * 128-thread kernel at three CTAs per SM, on a stream forked from and joined
+ * back to the caller's), 256 (two CTAs per SM) or 512 (any length). */
 int nslct_batch_threads(nslct_batch_t batch);
 /* nslct_batch_set_threads -- pin the batched kernels' CTA size (128, 256 or
  * 512, else NSLCT_E_ARG). NSLCT_E_SIZE if some field has a line that size does
