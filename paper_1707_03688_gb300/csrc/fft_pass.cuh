@@ -1189,10 +1189,17 @@ __host__ __device__ __forceinline__ int pair_box_rows(int rows) {
   return rows / 2 < 256 ? rows / 2 : 256;
 }
 
+// CTA size of the pair kernel for lines of up to 2048 points: 128 threads, four
+// CTAs per SM (256 threads and two CTAs per SM for 4096-point lines, whose pair
+// takes 256 threads)
+#ifndef NSLCT_PAIR_SMALL_THREADS
+#define NSLCT_PAIR_SMALL_THREADS 128
+#endif
 template <int L> struct PairShape {
   static constexpr int E = 16;
   static constexpr int T = L / E;                 // threads per line pair
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = L <= 2048 ? NSLCT_PAIR_SMALL_THREADS : 256;
+  static constexpr int CTAS = 512 / THREADS;      // per SM (128 registers a thread)
   static constexpr int G = THREADS / T;           // line pairs per CTA
   static constexpr int P = 2 * G;                 // lines per CTA
   static constexpr int SH = pad_shift(E);
@@ -1202,7 +1209,7 @@ template <int L> struct PairShape {
   static constexpr int OSTG = NSLCT_PAIR_SPLIT_STORE ? G * (L / 2) : 0;
   static constexpr size_t SMEM_COL = SMEM + (size_t)OSTG * sizeof(float4);
   static_assert(is_pow2(L) && L >= 256 && L <= 4096, "pair kernel lengths");
-  static_assert(SMEM_COL <= 113 * 1024, "two CTAs per SM");
+  static_assert(CTAS * (SMEM_COL + 1024) <= 228 * 1024, "CTAS CTAs per SM");
   static_assert((LS * sizeof(float4)) % 128 == 0, "TMA destinations on 128-byte boundaries");
   static_assert(2 * (L + 8) <= 2 * LS, "row landing fits the pair region");
 };
@@ -1515,7 +1522,7 @@ __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, con
 // transforms are (1) forward, forward, (2) inverse, forward, (3) inverse,
 // inverse, (4) forward, inverse.
 template <int L, bool COL, int MODE = 0>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(PairShape<L>::THREADS, PairShape<L>::CTAS)
 pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out) {
   using Sh = PairShape<L>;
   using Fft = PairFft<L>;
@@ -1906,7 +1913,7 @@ inline int launch_one(const PassDesc& d, cudaStream_t s) {
       const int mode = NSLCT_PAIR_X2 ? x2_program(d, dx.x2) : 0;
       if (pair_mode_built<COL>(mode)) {
         const long long npanels = (long long)((nlines + Sh::P - 1) / Sh::P) * nb;
-        const int blocks = npanels < 2 * d.num_sms ? (int)npanels : 2 * d.num_sms;
+        const int blocks = npanels < Sh::CTAS * d.num_sms ? (int)npanels : Sh::CTAS * d.num_sms;
         const int box = pair_box_rows(d.Nx / 2);
         if (COL && (!encode_column_map_batched(&mi, d.in, d.Nx, d.Ny, 2, nb, d.in_bstride, box) ||
                     !encode_column_map_batched(&mo, d.out, d.Nx, d.Ny, 2, nb, d.out_bstride, box)))
