@@ -1,15 +1,14 @@
 // Batched passes: one persistent launch per pass covers every field of a batch
 // of fields with uneven sizes (each with its own ABCD plan).
 //
-// Work items are (field, panel) pairs, ordered largest line first; CTA b takes
-// items b, b + grid, b + 2 grid, ... (items hold near-equal sample counts, so
-// the static order balances, and every future item of a CTA is known). Each
-// item's panel is copied global -> shared with 16-byte cp.async while the CTA
-// still computes the previous item; the item's descriptor is copied to one of
-// three shared slots the same way one item earlier, and the item records are
-// read into registers further ahead, so that starting an item waits on no
-// global load but its panel. The line length (a template parameter in the
-// single-field kernels) is dispatched per item here. Five such launches make
+// Work items are (field, panel) pairs, ordered largest line first, and handed
+// out through an atomic counter, so a CTA that finishes a small panel takes
+// the next one. A CTA takes its item indices three items ahead of use, reads
+// the item records two ahead and copies the descriptors one ahead (cp.async,
+// three shared slots), so that starting an item waits on no global load but
+// its panel, which is copied global -> shared with 16-byte cp.async while the
+// CTA still computes the previous item. The line length (a template parameter
+// in the single-field kernels) is dispatched per item here. Five passes make
 // one batched transform; they can be captured into one CUDA graph.
 #pragma once
 
@@ -25,13 +24,14 @@ namespace nslct {
 // CTA configurations (the template parameter TH below): 512 threads (one CTA
 // per SM, every length), 256 threads (two CTAs per SM with independent
 // barriers, lines up to 2048: a panel needs at least two lines of L/E threads
-// each), 128 threads (four CTAs per SM) and kB3K (batch_common.h), 128 threads for 3*2^a lines
-// alone (three CTAs per SM). Packed configurations hold the same positions of
-// two lines in each thread as the two FP32x2 lanes (pair_x2.cuh, LineFftX2),
-// so a panel has twice the lines of its threads: 128 threads pack power-of-two
-// lines up to 2048 (16 positions per line, 3*2^a lines run one per thread),
-// kB3K packs 3*2^a lines up to 1536 (24 positions per line: the registers of
-// three CTAs per SM, not four).
+// each), 128 threads (four CTAs per SM) and kB3K (batch_common.h): 128 threads
+// for 3*2^a lines alone (three CTAs per SM). Packed configurations hold the
+// same positions of two lines in each thread as the two FP32x2 lanes
+// (pair_x2.cuh, LineFftX2), so a panel has twice the lines of its threads:
+// 128 threads pack power-of-two lines up to 2048 (16 positions per line;
+// 3*2^a lines run one per thread), kB3K packs 3*2^a lines up to 1536 (24
+// positions per line: the registers of three CTAs per SM, not four).
+// bthreads gives a configuration's thread count.
 __host__ __device__ constexpr int bthreads(int TH) { return TH % 1000; }
 template <int L> __host__ __device__ constexpr bool x2_3k_length() {
   if constexpr (is_pow2(L) || L % 24 != 0 || L > 2048) return false;
