@@ -2162,7 +2162,7 @@ template <typename R, int L> struct DualShape {
 };
 
 template <typename R, int L, bool COL>
-__global__ void __launch_bounds__(DualShape<R, L>::THREADS, DualShape<R, L>::THREADS <= 128 ? 4 : (DualShape<R, L>::THREADS <= 256 ? 2 : 1))
+__global__ void __launch_bounds__(DualShape<R, L>::THREADS, DualShape<R, L>::THREADS <= 256 ? 2 : 1)
 dual_pass_kernel(PassDesc d, const void* in_y, void* out_y, double* partials, int accumulate) {
   using Sh = DualShape<R, L>;
   constexpr int E = Sh::E;

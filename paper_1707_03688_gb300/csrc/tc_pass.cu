@@ -82,7 +82,8 @@ constexpr uint32_t OFF_X = OFF_A + 4 * A_BYTES;  // scratch
 // barriers: table, mma_done[2], drain[NWARP]
 constexpr int BAR_TAB = 0, BAR_DONE = 1, BAR_DRAIN = 3, NBAR = 3 + NWARP;
 // then: TMEM base, abort flag, arrival counters [2]; then two buffers of the
-// scale exchange, each [4][128] quarter-row maxima and [NWARP] warp maxima
+// scale exchange, each [4][128] quarter-row maxima and [NWARP][2] per-line
+// warp maxima
 constexpr uint32_t OFF_SCALE = OFF_X + NBAR * 8 + 16;
 constexpr uint32_t SCALE_FLOATS = 4 * 128 + 2 * NWARP;
 constexpr uint32_t SMEM = OFF_SCALE + 2 * SCALE_FLOATS * 4;
