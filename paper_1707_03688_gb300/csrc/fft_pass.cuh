@@ -1399,6 +1399,106 @@ template <int L> struct X2Fft {
   }
 };
 
+#ifndef NSLCT_X2_HALFWARP
+#define NSLCT_X2_HALFWARP 1
+#endif
+// A pair of 4096-point line-pair FFTs with one CTA-wide exchange each (the
+// two transforms of a column pass or of row pass 3). With n = n0 + 16 n1 + 256
+// n2 and k = k0 + 16 k1 + 256 k2, nk = 256 n2 k0 + 16 n1 (k0 + 16 k1) + n0 (k0
+// + 16 k1 + 256 k2) mod 4096, so the first transform runs
+//   A  thread n0 + 16 n1 (natural order): DFT-16 over n2 -> k0;
+//   B  thread 16 k0 + n0: twiddle W_256^{n1 k0}, DFT-16 over n1 -> k1;
+//   C  thread 16 k0 + k1: twiddle W_4096^{n0 (k0 + 16 k1)}, DFT-16 over n0 -> k2,
+// leaving thread t with X[sw(t) + 256 k2], sw(t) = (t >> 4) + 16 (t & 15).
+// A -> B is an all-to-all (CTA barriers); B -> C stays inside the half-warp of
+// k0, in the very entries that half-warp read in A -> B, so it needs only
+// __syncwarp. The second transform is the transpose of the first (the DFT
+// matrix is symmetric): from that swapped order back to the natural one, the
+// half-warp exchange first and the all-to-all last, each twiddle after its
+// DFT. Two CTA barriers per transform instead of four; the twiddle bases are
+// the compact table's stage 1 and 2 entries.
+struct X2Fft4096H {
+  static constexpr int L = 4096;
+  static constexpr int E = 16;
+  static constexpr int SH = pad_shift(E);
+  static __device__ __forceinline__ int sw(int t) { return (t >> 4) + 16 * (t & 15); }
+  static __device__ __forceinline__ int px(int p) { return padded_by<SH>(p); }
+  static __device__ __forceinline__ float2 w256(const float2* __restrict__ tw, int j) {
+    return __ldg(tw + compact_table_offset(L, E, 1) + j);
+  }
+  static __device__ __forceinline__ float2 w4096(const float2* __restrict__ tw, int j) {
+    return __ldg(tw + compact_table_offset(L, E, 2) + j);
+  }
+
+  // v: the thread's elements t + 256 s; on return X[sw(t) + 256 s].
+  static __device__ __forceinline__ void run_b(cx2* v, ulonglong2* sm, int t, const float2* __restrict__ tw) {
+    const X2Const K;
+    X2Dft<16>::run(v, K);  // A: over n2
+    const int n0 = t & 15, n1 = t >> 4;
+    __syncthreads();  // the previous user of `sm` is done
+#pragma unroll
+    for (int k0 = 0; k0 < 16; ++k0) sm[px(256 * k0 + 16 * n0 + n1)] = make_ulonglong2(v[k0].re, v[k0].im);
+    __syncthreads();
+    const int k0 = t >> 4, m = t & 15;  // B: this thread is (k0, n0 = m)
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const ulonglong2 q = sm[px(256 * k0 + 16 * m + r)];
+      v[r] = cx2{q.x, q.y};
+    }
+    x2_twiddle_scalar_powers<16>(v, w256(tw, k0));
+    X2Dft<16>::run(v, K);
+    __syncwarp();  // the half-warp has read its entries; they now take its B -> C exchange
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) sm[px(256 * k0 + 16 * k1 + m)] = make_ulonglong2(v[k1].re, v[k1].im);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {  // C: this thread is (k0, k1 = m)
+      const ulonglong2 q = sm[px(256 * k0 + 16 * m + r)];
+      v[r] = cx2{q.x, q.y};
+    }
+    x2_twiddle_scalar_powers<16>(v, w4096(tw, k0 + 16 * m));
+    X2Dft<16>::run(v, K);
+  }
+
+  // v: the thread's elements sw(t) + 256 s, the order run_b leaves (its
+  // half-warp's entries of `sm` last touched by its own run_b); on return the
+  // transform's elements t + 256 s. With `call`, freed() runs in every thread
+  // after a barrier once the buffer has been read for the last time.
+  template <class Hook>
+  static __device__ __forceinline__ void run_t(cx2* v, ulonglong2* sm, int t, const float2* __restrict__ tw,
+                                               const Hook& freed, bool call) {
+    const X2Const K;
+    const int k0 = t >> 4, m = t & 15;  // C^T: this thread is (k0, k1 = m)
+    X2Dft<16>::run(v, K);                // over k2 -> n0
+    x2_twiddle_scalar_powers<16>(v, w4096(tw, k0 + 16 * m));
+    __syncwarp();
+#pragma unroll
+    for (int n0 = 0; n0 < 16; ++n0) sm[px(256 * k0 + 16 * n0 + m)] = make_ulonglong2(v[n0].re, v[n0].im);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {  // B^T: this thread is (k0, n0 = m)
+      const ulonglong2 q = sm[px(256 * k0 + 16 * m + r)];
+      v[r] = cx2{q.x, q.y};
+    }
+    X2Dft<16>::run(v, K);  // over k1 -> n1
+    x2_twiddle_scalar_powers<16>(v, w256(tw, k0));
+    __syncthreads();  // every half-warp has read its entries
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) sm[px(256 * n1 + 16 * m + k0)] = make_ulonglong2(v[n1].re, v[n1].im);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {  // A^T: this thread is (n0, n1) = (t & 15, t >> 4)
+      const ulonglong2 q = sm[px(16 * t + r)];
+      v[r] = cx2{q.x, q.y};
+    }
+    if (call) {
+      __syncthreads();  // every thread has read the buffer for the last time
+      freed();
+    }
+    X2Dft<16>::run(v, K);  // over k0 -> n2
+  }
+};
+
 // One step of a packed pass program on the thread's E positions of lines
 // line0 and line0 + 1: multiply by the chirp (its phases exactly as in
 // apply_chirp_c, one Q0.64 phase per line) times scale, or by scale alone.
@@ -1592,6 +1692,8 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       }
     };
     float2 v0[E], v1[E];
+    int eb = t;            // the thread's elements are eb + T s
+    bool swapped = false;  // eb = X2Fft4096H::sw(t), between the two transforms of a pair
     if (COL) {
 #pragma unroll
       for (int s = 0; s < E; ++s) {
@@ -1679,19 +1781,39 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         const f32x2 re = x2_pack(v0[s].x, v1[s].x), im = x2_pack(v0[s].y, v1[s].y);
         v[s] = FINV ? cx2{im, re} : cx2{re, im};
       }
-      if (d.x2.pre.kind) x2_step<L, COL, false>(v, d.x2.pre, FINV, d, t, line0);
+      if (d.x2.pre.kind) x2_step<L, COL, false>(v, d.x2.pre, FINV, d, eb, line0);
       ulonglong2* xs2 = reinterpret_cast<ulonglong2*>(xs);
 #pragma unroll 1
       for (int k = 0; k < d.x2.ntr; ++k) {
         if (k > 0) {
           // the gap after transform k-1, whose domain is J when it was an inverse
           const X2Step st = k == 1 ? d.x2.gap[0] : d.x2.gap[1];
-          x2_step<L, COL, true>(v, st, FINV != (((k - 1) & 1) != 0), d, t, line0);
+          x2_step<L, COL, true>(v, st, FINV != (((k - 1) & 1) != 0), d, eb, line0);
         }
-        X2Fft<L>::run(v, xs2, t, g, tw, load_next, EARLY && k == d.x2.ntr - 1);
+        const bool early = EARLY && k == d.x2.ntr - 1;
+        if constexpr (L == 4096 && NSLCT_X2_HALFWARP && !COL && MODE == 2) {
+          // row pass 3's two transforms: X2Fft4096H's pair (natural -> swapped
+          // -> natural); a lone one, or the third of three: the Stockham FFT.
+          // (Measured: row pass 3 at 4096^2 89.0 against 92.4 us; the column
+          // pass's pair gained nothing, 95.9 against 95.5 us, and compiling the
+          // pair into the one-transform passes' kernels slowed them by 3-4 us.)
+          if (swapped) {
+            X2Fft4096H::run_t(v, xs2, t, tw, load_next, early);
+            eb = t;
+            swapped = false;
+          } else if (k + 1 < d.x2.ntr) {
+            X2Fft4096H::run_b(v, xs2, t, tw);
+            eb = X2Fft4096H::sw(t);
+            swapped = true;
+          } else {
+            X2Fft<L>::run(v, xs2, t, g, tw, load_next, early);
+          }
+        } else {
+          X2Fft<L>::run(v, xs2, t, g, tw, load_next, early);
+        }
       }
-      if (d.x2.post[0].kind) x2_step<L, COL, false>(v, d.x2.post[0], LINV, d, t, line0);
-      if (d.x2.post[1].kind) x2_step<L, COL, false>(v, d.x2.post[1], LINV, d, t, line0);
+      if (d.x2.post[0].kind) x2_step<L, COL, false>(v, d.x2.post[0], LINV, d, eb, line0);
+      if (d.x2.post[1].kind) x2_step<L, COL, false>(v, d.x2.post[1], LINV, d, eb, line0);
 #pragma unroll
       for (int s = 0; s < E; ++s) {
         const cx2 w = LINV ? cx2{v[s].im, v[s].re} : v[s];
@@ -1702,8 +1824,8 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
     if (!COL && !d.out_tiled && d.post_mask) {
 #pragma unroll
       for (int s = 0; s < E; ++s) {
-        v0[s] = apply_post_mask<float>(d, line0, t + T * s, v0[s]);
-        v1[s] = apply_post_mask<float>(d, line0 + 1, t + T * s, v1[s]);
+        v0[s] = apply_post_mask<float>(d, line0, eb + T * s, v0[s]);
+        v1[s] = apply_post_mask<float>(d, line0 + 1, eb + T * s, v1[s]);
       }
     }
     if constexpr (!EARLY) __syncthreads();  // every thread has finished reading the buffer
@@ -1716,7 +1838,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-          const int e = t + T * s;
+          const int e = eb + T * s;
           o4[((size_t)(e >> 1) * (2 * d.Ny) + (line0 >> 1) * 4 + (e & 1) * 2) >> 1] =
               make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
         }
@@ -1727,7 +1849,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       float4* ostg = xs + Sh::G * Sh::LS;
 #pragma unroll
       for (int s = 0; s < E; ++s) {
-        const int e = t + T * s;
+        const int e = eb + T * s;
         const float4 q = make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
         if (e < L / 2) ostg[g * (L / 2) + e] = q;
         else xg[e] = q;
@@ -1755,7 +1877,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
       // leave through the buffer: the box layout is (line0[e], line1[e]) per e
 #pragma unroll
       for (int s = 0; s < E; ++s)
-        xg[t + T * s] = make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
+        xg[eb + T * s] = make_float4(v0[s].x, v0[s].y, v1[s].x, v1[s].y);
       fence_proxy_async();
       __syncthreads();
       if (tid == 0) {
@@ -1777,7 +1899,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         const int r = line0 - d.out_r0;
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-          const int c = t + T * s - d.out_c0;
+          const int c = eb + T * s - d.out_c0;
           if ((unsigned)c < (unsigned)d.out_cols) {
             if ((unsigned)r < (unsigned)d.out_rows) out[(size_t)r * d.out_cols + c] = v0[s];
             if ((unsigned)(r + 1) < (unsigned)d.out_rows) out[(size_t)(r + 1) * d.out_cols + c] = v1[s];
@@ -1789,14 +1911,17 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
         // from the even lane and (line1[e-1], line1[e]) from the odd one
         // (every lane shuffles: with 16 threads per pair a warp can straddle
         // a valid and an invalid pair)
-        const bool odd = (t & 1) != 0;
+        // (the neighbouring element's thread: lane ^ 1, or lane ^ 16 in the
+        // swapped order of X2Fft4096H)
+        const bool odd = (eb & 1) != 0;
+        const int pm = swapped ? 16 : 1;
         float4* o4 = reinterpret_cast<float4*>(d.out_tiled ? out + (size_t)(line0 >> 1) * (2 * L)
                                                            : out + (size_t)line0 * L);
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-          const int e = t + T * s;
+          const int e = eb + T * s;
           const float2 give = odd ? v0[s] : v1[s];
-          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, give.x, 1), __shfl_xor_sync(0xffffffffu, give.y, 1));
+          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, give.x, pm), __shfl_xor_sync(0xffffffffu, give.y, pm));
           const float4 q = odd ? make_float4(got.x, got.y, v1[s].x, v1[s].y) : make_float4(v0[s].x, v0[s].y, got.x, got.y);
           if (valid) o4[d.out_tiled ? e : (odd ? (L + e - 1) / 2 : e / 2)] = q;
         }
@@ -1805,7 +1930,7 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
           float2* o = out + (size_t)(line0 >> 1) * (2 * L);
 #pragma unroll
           for (int s = 0; s < E; ++s) {
-            const int e = t + T * s;
+            const int e = eb + T * s;
             o[(e >> 1) * 4 + (e & 1)] = v0[s];
             o[(e >> 1) * 4 + 2 + (e & 1)] = v1[s];
           }
@@ -1813,8 +1938,8 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
           float2* o = out + (size_t)line0 * L;
 #pragma unroll
           for (int s = 0; s < E; ++s) {
-            o[t + T * s] = v0[s];
-            o[L + t + T * s] = v1[s];
+            o[eb + T * s] = v0[s];
+            o[L + eb + T * s] = v1[s];
           }
         }
       }
