@@ -53,7 +53,7 @@ NCU_TRAFFIC = {"pass_kernel_pair<4096, 0, 1>": 213.2e6, "pass_kernel_pair<4096, 
 PASS_KERNELS = {
     ("fp32", 5): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 2>",
                   "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
-    ("fp32", 3): ["pass_kernel_pair<4096, 0, 1>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
+    ("fp32", 3): ["pass_kernel_pair<4096, 0, 5>", "pass_kernel_pair<4096, 1, 4>", "pass_kernel_pair<4096, 0, 3>"],
     ("mixed", 5): ["pass_kernel_tc<0>", "pass_kernel_tc<1>", "pass_kernel_tc<0>", "pass_kernel_tc<1>",
                    "pass_kernel_tc<0>"],
     ("mixed", 3): ["pass_kernel_tc<0>", "pass_kernel_tc<1>", "pass_kernel_tc<0>"],

@@ -1620,7 +1620,8 @@ __device__ __forceinline__ void pair_load_panel(float4* x, const float2* in, con
 // MODE 0: scalar arithmetic, any sequence of transforms. MODE 1..4: packed
 // FP32x2 (pair_x2.cuh) running the pass program d.x2, whose first and last
 // transforms are (1) forward, forward, (2) inverse, forward, (3) inverse,
-// inverse, (4) forward, inverse.
+// inverse, (4) forward, inverse; MODE 5 is mode 1 for programs of more than
+// one transform (4096-point rows: their first two run as X2Fft4096H's pair).
 template <int L, bool COL, int MODE = 0>
 __global__ void __launch_bounds__(PairShape<L>::THREADS, PairShape<L>::CTAS)
 pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out) {
@@ -1791,12 +1792,14 @@ pass_kernel_pair(PassDesc d, const __grid_constant__ CUtensorMap map_in, const _
           x2_step<L, COL, true>(v, st, FINV != (((k - 1) & 1) != 0), d, eb, line0);
         }
         const bool early = EARLY && k == d.x2.ntr - 1;
-        if constexpr (L == 4096 && NSLCT_X2_HALFWARP && !COL && MODE == 2) {
-          // row pass 3's two transforms: X2Fft4096H's pair (natural -> swapped
-          // -> natural); a lone one, or the third of three: the Stockham FFT.
-          // (Measured: row pass 3 at 4096^2 89.0 against 92.4 us; the column
-          // pass's pair gained nothing, 95.9 against 95.5 us, and compiling the
-          // pair into the one-transform passes' kernels slowed them by 3-4 us.)
+        if constexpr (L == 4096 && NSLCT_X2_HALFWARP && !COL && (MODE == 2 || MODE == 5)) {
+          // row passes of two or more transforms (mode 2, and mode 5: mode 1's
+          // program with more than one transform): X2Fft4096H's pair (natural
+          // -> swapped -> natural); a lone one, or the third of three: the
+          // Stockham FFT. (Measured: row pass 3 at 4096^2 89.0 against 92.4 us;
+          // the column pass's pair gained nothing, 95.9 against 95.5 us, and
+          // compiling the pair into the one-transform passes' kernels slowed
+          // them by 3-4 us, hence the separate mode 5.)
           if (swapped) {
             X2Fft4096H::run_t(v, xs2, t, tw, load_next, early);
             eb = t;
@@ -2045,7 +2048,14 @@ inline int launch_one(const PassDesc& d, cudaStream_t s) {
           return NSLCT_E_CUDA;
         if constexpr (!NSLCT_PAIR_X2) launch_pair<L, COL, 0>(dx, mi, mo, blocks, s);
         else if constexpr (COL) launch_pair<L, true, 4>(dx, mi, mo, blocks, s);
-        else if (mode == 1) launch_pair<L, false, 1>(dx, mi, mo, blocks, s);
+        else if (mode == 1) {
+          if constexpr (L == 4096 && NSLCT_X2_HALFWARP) {
+            if (dx.x2.ntr > 1) launch_pair<L, false, 5>(dx, mi, mo, blocks, s);
+            else launch_pair<L, false, 1>(dx, mi, mo, blocks, s);
+          } else {
+            launch_pair<L, false, 1>(dx, mi, mo, blocks, s);
+          }
+        }
         else if (mode == 2) launch_pair<L, false, 2>(dx, mi, mo, blocks, s);
         else launch_pair<L, false, 3>(dx, mi, mo, blocks, s);
         return cudaGetLastError() == cudaSuccess ? NSLCT_OK : NSLCT_E_CUDA;
@@ -2089,6 +2099,8 @@ inline int prepare_one() {
     if constexpr (NSLCT_PAIR && is_pow2(L) && L >= 256) {
       if constexpr (NSLCT_PAIR_X2) {
         if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 1>();
+        if constexpr (L == 4096 && NSLCT_X2_HALFWARP)
+          if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 5>();
         if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 2>();
         if (e1 == cudaSuccess) e1 = prepare_pair<L, false, 3>();
         if (e2 == cudaSuccess) e2 = prepare_pair<L, true, 4>();
