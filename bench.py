@@ -46,7 +46,8 @@ BYTES_PER_SAMPLE_PASS = 16        # read + write one complex64 per sample per pa
 # current FP32 pass kernels (one full capture of one forward transform; the
 # column kernel: the mean of passes 2 and 4). Reset whenever a kernel changes.
 NCU_TRAFFIC = {"pass_kernel_pair<4096, 0, 1>": 213.2e6, "pass_kernel_pair<4096, 1, 4>": 214.8e6,
-               "pass_kernel_pair<4096, 0, 2>": 207.9e6, "pass_kernel_pair<4096, 0, 3>": 208.0e6}
+               "pass_kernel_pair<4096, 0, 2>": 207.9e6, "pass_kernel_pair<4096, 0, 3>": 208.0e6,
+               "pass_kernel_pair<4096, 0, 5>": 212.5e6}
 # the kernel (as ncu names it) that runs each pass of the forward transform:
 # the line-pair kernel's template arguments are (length, column pass, mode),
 # the mode naming the first and last transform directions of the pass
